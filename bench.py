@@ -1,0 +1,466 @@
+#!/usr/bin/env python
+"""Benchmark of the energy-minimisation prolongation loop on one GB300.
+
+Workload: 3D 7-point finite-volume diffusion on a 128^3 grid (2,097,152 rows,
+14,581,760 entries of A) with log-normal cell coefficients (sigma = 2,
+seed 2), constant near kernel (k = 1), 3x3x3 aggregates (74,088 coarse
+dofs), P pattern = pattern of A P0 (6,127,616 entries), 20 restricted PCG
+iterations.  One step = one whole minimisation with the inputs resident in
+HBM: set-up (Gram factorisation, constraint correction of P0, initial
+residual), 20 iterations (masked product + projection + reductions +
+Jacobi/vector updates), and the final prolongation P (in mixed precision
+with its double-precision constraint restore).
+
+Metric: restricted-PCG iterations/s (20 per step) of the whole job; the
+dominant kernel (the masked product with fused projection) is reported
+against the HBM roofline.  The headline line is the mixed (float bulk)
+path; the plain FP64 path is reported beside it in the same line.
+
+  python bench.py [--gpus N] [--steps K] [--warmup W] [--impl ours|reference]
+
+Several GPUs run independent replicas (the method is not sharded here):
+value = iterations of all ranks / max-over-ranks time.
+"""
+from __future__ import annotations
+
+import argparse
+import json
+import os
+import subprocess
+import sys
+import time
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+if ROOT not in sys.path:
+    sys.path.insert(0, ROOT)
+
+METRIC = ("restricted-PCG iterations/s and masked A·P effective HBM GB/s "
+          "(% of peak), FP32 vs FP64")
+WORKLOAD = 2
+ITERS = 20
+FP64_PEAK_TFLOPS = 1.25  # nominal GB300 FP64 (no measured FP64 peak on this machine)
+
+
+def parse():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=10)
+    ap.add_argument("--warmup", type=int, default=3)
+    ap.add_argument("--impl", choices=["ours", "reference"], default="ours")
+    ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--no-e2e", action="store_true")
+    ap.add_argument("--precision", choices=["both", "mixed", "fp64"], default="both",
+                    help="profiling aid: run one arm only (the JSON line needs both)")
+    return ap.parse_args()
+
+
+# ---------------------------------------------------------------------------
+# distributed plumbing (replicas only; a host-side max of the times)
+# ---------------------------------------------------------------------------
+class Dist:
+    def __init__(self):
+        self.world = int(os.environ.get("WORLD_SIZE", "1"))
+        self.rank = int(os.environ.get("RANK", "0"))
+        self.local = int(os.environ.get("LOCAL_RANK", "0"))
+        self.pg = None
+        if self.world > 1:
+            import torch.distributed as dist
+            os.environ.setdefault("MASTER_ADDR", "127.0.0.1")
+            dist.init_process_group("gloo")
+            self.pg = dist
+
+    def barrier(self):
+        if self.pg:
+            self.pg.barrier()
+
+    def max(self, x: float) -> float:
+        if not self.pg:
+            return x
+        import torch
+        t = torch.tensor([x], dtype=torch.float64)
+        self.pg.all_reduce(t, op=self.pg.ReduceOp.MAX)
+        return float(t.item())
+
+    def close(self):
+        if self.pg:
+            self.pg.destroy_process_group()
+
+
+# ---------------------------------------------------------------------------
+# algorithmic work of one masked-product launch (Section 4; k = 1 here)
+# ---------------------------------------------------------------------------
+def kprod_bytes(prob, vbytes: int) -> int:
+    """A (values + column indices + row pointers), P's pattern, Y read once,
+    Y_ written once, the per-row inverse Gram factor and B_c."""
+    n, k = prob.n, prob.k
+    a = prob.nnz_a * (vbytes + 4) + 4 * (n + 1)
+    pat = 4 * prob.nnz_p + 4 * (n + 1)
+    vec = 2 * vbytes * prob.nnz_p
+    fac = n * (k * (k + 1) // 2) * vbytes + prob.nc * k * vbytes
+    return a + pat + vec + fac
+
+
+def in_pattern_products(prob) -> tuple[int, int]:
+    """(candidate products, products landing in P's pattern) of one
+    mask_P(A Y), counted on the host from the two patterns."""
+    import numpy as np
+    n = prob.n
+    m = np.diff(prob.P_rowptr)
+    w = int(m.max())
+    J = np.full((n, w), -1, dtype=np.int64)
+    rows = np.repeat(np.arange(n), m)
+    pos = np.arange(prob.nnz_p) - prob.P_rowptr[rows]
+    J[rows, pos] = prob.P_col
+    arow = np.repeat(np.arange(n), np.diff(prob.A_rowptr))
+    cand = int(m[prob.A_col].sum())
+    hits = 0
+    for s0 in range(0, prob.nnz_a, 1 << 22):
+        i = arow[s0:s0 + (1 << 22)]
+        l = prob.A_col[s0:s0 + (1 << 22)]
+        Ji, Jl = J[i], J[l]
+        eq = (Ji[:, :, None] == Jl[:, None, :]) & (Ji[:, :, None] >= 0)
+        hits += int(eq.sum())
+    return cand, hits
+
+
+def kprod_flops(prob, hits: int) -> int:
+    """FP64 flops of one masked product with projection and y^T y_:
+    2 per in-pattern product, 4 k per entry of P (B_i^T x and x - B_i c),
+    2 k^2 per row (G_i^{-1} t) and 2 per entry (the dot)."""
+    k = prob.k
+    return 2 * hits + 4 * k * prob.nnz_p + 2 * k * k * prob.n + 2 * prob.nnz_p
+
+
+# ---------------------------------------------------------------------------
+# clocks during the timed region
+# ---------------------------------------------------------------------------
+class Clocks:
+    Q = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+         "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+         "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, index: int):
+        self.index = index
+        self.proc = None
+        self.path = None
+
+    def start(self):
+        import tempfile
+        try:
+            fd, self.path = tempfile.mkstemp(suffix=".csv")
+            os.close(fd)
+            self.proc = subprocess.Popen(
+                ["nvidia-smi", f"--id={self.index}", f"--query-gpu={self.Q}",
+                 "--format=csv,noheader,nounits", "-lms", "100"],
+                stdout=open(self.path, "w"), stderr=subprocess.DEVNULL)
+        except (OSError, FileNotFoundError):
+            self.proc = None
+
+    def stop(self):
+        if not self.proc:
+            return None
+        self.proc.terminate()
+        try:
+            self.proc.wait(timeout=5)
+        except subprocess.TimeoutExpired:
+            self.proc.kill()
+        sm, mx, reasons = [], 0.0, set()
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        with open(self.path) as f:
+            for line in f:
+                p = [x.strip() for x in line.split(",")]
+                if len(p) < 9:
+                    continue
+                try:
+                    sm.append(float(p[1]))
+                    mx = max(mx, float(p[2]))
+                except ValueError:
+                    continue
+                for nm, v in zip(names, p[5:9]):
+                    if v.lower() == "active":
+                        reasons.add(nm)
+        os.unlink(self.path)
+        if not sm:
+            return None
+        sm.sort()
+        return {"sm_mhz": sm[len(sm) // 2], "sm_max_mhz": mx, "reasons": sorted(reasons),
+                "samples": len(sm)}
+
+
+# ---------------------------------------------------------------------------
+# our arm
+# ---------------------------------------------------------------------------
+def time_steps(ctx, out, K, W, stream, dist):
+    """W untimed steps, then K timed steps; CUDA events on the library's
+    stream, barrier + synchronize on both sides."""
+    import torch
+
+    def step():
+        ctx.reset()
+        ctx.iterate(ITERS, 0.0)
+        ctx.get_p(out)
+
+    for _ in range(W):
+        step()
+    torch.cuda.synchronize()
+    dist.barrier()
+    t0 = torch.cuda.Event(enable_timing=True)
+    t1 = torch.cuda.Event(enable_timing=True)
+    t0.record(stream)
+    for _ in range(K):
+        step()
+    t1.record(stream)
+    torch.cuda.synchronize()
+    dist.barrier()
+    return t0.elapsed_time(t1)
+
+
+def run_ours(args, dist):
+    import numpy as np
+    import torch
+
+    from paper_2208_02995_gb300 import inputs
+    from paper_2208_02995_gb300.emin import (Context, emin_set_timing, emin_timing)
+
+    torch.cuda.set_device(dist.local)
+    prob = inputs.config(WORKLOAD)
+    peaks = {}
+    try:
+        with open(os.path.join(ROOT, "MEASURED_PEAKS.json")) as f:
+            peaks = json.load(f)
+    except OSError:
+        pass
+    hbm_peak = float(peaks.get("hbm_gbs", 6800.0))
+    hbm_src = "measured" if "hbm_gbs" in peaks else "fallback"
+
+    cand, hits = in_pattern_products(prob)
+    stream = torch.cuda.Stream()
+    results = {}
+    precs = ("mixed", "fp64") if args.precision == "both" else (args.precision,)
+    for prec in precs:
+        with torch.cuda.stream(stream):
+            ctx = Context(prob, precision=prec, stream=stream)
+            out = torch.empty(prob.nnz_p, dtype=torch.float64, device="cuda")
+        clocks = Clocks(dist.local) if prec == "mixed" else None
+        l0 = emin_timing(ctx.h)["total_launches"]
+        # the timed region also times every kernel launch of the iteration
+        emin_set_timing(ctx.h, True)
+        if clocks:
+            clocks.start()
+        ms = time_steps(ctx, out, args.steps, args.warmup, stream, dist)
+        clk = clocks.stop() if clocks else None
+        tm = emin_timing(ctx.h)
+        emin_set_timing(ctx.h, False)
+        launches = tm["total_launches"] - l0
+        per_step_launches = launches / (args.steps + args.warmup)
+        ms_max = dist.max(ms)
+        kprod_avg_s = tm["ms"][0] / max(tm["launches"][0], 1) / 1e3
+        results[prec] = {
+            "ms": ms_max, "clocks": clk,
+            "gpu_launches": int(round(per_step_launches * args.steps)),
+            "kprod_avg_us": kprod_avg_s * 1e6,
+            "kernel_share": {"kprod": tm["ms"][0], "ydir": tm["ms"][1], "update": tm["ms"][2]},
+            "P": out.cpu().numpy(),
+        }
+        ctx.close()
+    if args.precision != "both":
+        r = results[args.precision]
+        return {"precision": args.precision, "ms_per_step": r["ms"] / args.steps,
+                "kprod_avg_us": r["kprod_avg_us"], "kernel_ms": r["kernel_share"],
+                "gpu_launches": r["gpu_launches"]}
+    # end-to-end through the C ABI from pinned host buffers
+    e2e = None
+    if not args.no_e2e:
+        e2e = run_e2e(prob, args, dist)
+
+    m = results["mixed"]
+    K = args.steps
+    value = dist.world * ITERS * K / (m["ms"] / 1e3)
+    b32 = kprod_bytes(prob, 4)
+    ach = b32 / (m["kprod_avg_us"] * 1e-6) / 1e9
+    f = results["fp64"]
+    fl = kprod_flops(prob, hits)
+    ach64 = fl / (f["kprod_avg_us"] * 1e-6) / 1e12
+    b64 = kprod_bytes(prob, 8)
+    line = {
+        "metric": METRIC,
+        "value": value,
+        "unit": "iterations/s",
+        "n_gpus": dist.world,
+        "steps": K,
+        "warmup": args.warmup,
+        "ms_per_step": m["ms"] / K,
+        "higher_is_better": True,
+        "scaling": "weak",
+        "vs_baseline": None,
+        "dtype": "f32",
+        "data": "synthetic",
+        "config": {
+            "workload": ("3D 7-point FV diffusion 128^3 (n=2,097,152, nnz(A)=14,581,760), "
+                         "log-normal kappa sigma=2 seed 2, k=1, 3x3x3 aggregates "
+                         "(n_c=74,088), nnz(P)=6,127,616, 20 restricted PCG iterations"),
+            "step": "set-up + 20 iterations + final P, inputs resident in HBM",
+            "precision": "mixed: float A/P/products, double Gram factorisation, "
+                         "reductions and final constraint restore",
+            "l2": "inputs larger than L2 (A 175 MB + P vectors 123 MB > 129 MB)",
+            "parallelism": f"replicas x{dist.world}",
+            "candidate_products": cand,
+            "in_pattern_products": hits,
+        },
+        "roofline": {
+            "kernel": "masked product + projection + y^T y_ (k_kprod_row_k1<float,4>)",
+            "bound": "hbm",
+            "achieved": ach,
+            "peak": hbm_peak,
+            "unit": "GB/s",
+            "frac": ach / hbm_peak,
+            "traffic": None,
+            "algorithmic_bytes": b32,
+            "avg_launch_us": m["kprod_avg_us"],
+            "peak_source": hbm_src,
+        },
+        "fp64": {
+            "value": dist.world * ITERS * K / (f["ms"] / 1e3),
+            "unit": "iterations/s",
+            "ms_per_step": f["ms"] / K,
+            "dtype": "f64",
+            "roofline": {
+                "kernel": "masked product + projection + y^T y_ (k_kprod_row_k1<double,4>)",
+                "bound": "alu",
+                "achieved": ach64,
+                "peak": FP64_PEAK_TFLOPS,
+                "unit": "TFLOP/s",
+                "frac": ach64 / FP64_PEAK_TFLOPS,
+                "traffic": None,
+                "flops": fl,
+                "hbm_gbs": b64 / (f["kprod_avg_us"] * 1e-6) / 1e9,
+                "avg_launch_us": f["kprod_avg_us"],
+                "peak_source": "nominal FP64 rate of GB300 (152 SMs x 2 FP64 FMA/clk x 2070 MHz)",
+            },
+            "gpu_launches": f["gpu_launches"],
+        },
+        "kernel_ms": {p: results[p]["kernel_share"] for p in results},
+        "gpu_launches": m["gpu_launches"],
+        "clocks": m["clocks"],
+        "e2e": e2e,
+        "mixed_vs_fp64": {
+            "P_rel_diff": float(np.linalg.norm(results["mixed"]["P"] - results["fp64"]["P"]) /
+                                np.linalg.norm(results["fp64"]["P"])),
+            "time_to_P_ratio": f["ms"] / m["ms"],
+        },
+    }
+    if dist.world == 1 and not args.no_cpu_baseline and dist.rank == 0:
+        line["cpu_baseline"] = cpu_baseline(prob)
+    return line
+
+
+def run_e2e(prob, args, dist):
+    """Same metric through the C ABI with host buffers: every step creates a
+    context from pinned host arrays (H2D copies), iterates, reads P back to
+    pinned host memory (D2H) and destroys the context."""
+    import numpy as np
+    import torch
+
+    from paper_2208_02995_gb300.emin import Context
+
+    pinned = []
+    for a in prob.arrays():
+        t = torch.from_numpy(np.ascontiguousarray(a)).pin_memory()
+        pinned.append(t.numpy())
+    out = torch.empty(prob.nnz_p, dtype=torch.float64).pin_memory().numpy()
+    h2d = sum(a.nbytes for a in pinned)
+    d2h = out.nbytes
+    K = max(1, min(args.steps, 5))
+
+    def step():
+        c = Context(n=prob.n, nc=prob.nc, k=prob.k, arrays=pinned, precision="mixed",
+                    on_device=False)
+        c.iterate(ITERS, 0.0)
+        c.get_p(out)
+        c.close()
+
+    step()
+    torch.cuda.synchronize()
+    dist.barrier()
+    t = time.perf_counter()
+    for _ in range(K):
+        step()
+    torch.cuda.synchronize()
+    el = dist.max(time.perf_counter() - t)
+    return {"value": dist.world * ITERS * K / el, "unit": "iterations/s",
+            "h2d_bytes_per_step": int(h2d), "d2h_bytes_per_step": int(d2h),
+            "steps": K, "precision": "mixed"}
+
+
+def cpu_baseline(prob):
+    """The FP64 oracle as it stands (single thread) on the host: one whole
+    minimisation (set-up + 20 iterations) of the same workload."""
+    from oracle.oracle import Oracle
+    t = time.perf_counter()
+    o = Oracle(prob)
+    o.minimize(ITERS, 0.0)
+    el = time.perf_counter() - t
+    return {"value": ITERS / el, "unit": "iterations/s", "cores": 1, "kind": "oracle",
+            "sample": "one whole minimisation (set-up + 20 iterations) of the 128^3 workload",
+            "seconds": el}
+
+
+# ---------------------------------------------------------------------------
+# reference arm: the oracle on the host cores
+# ---------------------------------------------------------------------------
+def run_reference(args, dist):
+    from oracle.oracle import Oracle
+    from paper_2208_02995_gb300 import inputs
+
+    prob = inputs.config(WORKLOAD)
+    # each step is one whole minimisation when K + W steps fit in ~4 minutes,
+    # else a bounded sample of fewer iterations (same set-up)
+    budget_s, est_step_s = 240.0, 12.0
+    its = ITERS if (args.steps + args.warmup) * est_step_s <= budget_s else \
+        max(1, int(ITERS * budget_s / ((args.steps + args.warmup) * est_step_s)))
+
+    def step():
+        o = Oracle(prob)
+        o.minimize(its, 0.0)
+
+    for _ in range(args.warmup):
+        step()
+    t = time.perf_counter()
+    for _ in range(args.steps):
+        step()
+    el = time.perf_counter() - t
+    value = its * args.steps / el
+    sample = (f"{'whole minimisation' if its == ITERS else 'sample'}: set-up + {its} iterations "
+              f"of the 128^3 workload per step, single-threaded FP64 oracle")
+    return {
+        "impl": "reference", "metric": METRIC, "value": value, "unit": "iterations/s",
+        "n_gpus": dist.world, "steps": args.steps, "warmup": args.warmup,
+        "ms_per_step": el / args.steps * 1e3, "higher_is_better": True, "scaling": "weak",
+        "vs_baseline": None, "dtype": "f64", "data": "synthetic",
+        "config": {"workload": "3D 7-point FV diffusion 128^3, k=1, 3x3x3 aggregates, "
+                               "20 restricted PCG iterations", "precision": "fp64 (oracle)"},
+        "cpu_baseline": {"value": value, "unit": "iterations/s", "cores": 1, "kind": "oracle",
+                         "sample": sample},
+        "e2e": {"value": value, "unit": "iterations/s", "h2d_bytes_per_step": 0,
+                "d2h_bytes_per_step": 0},
+        "gpu_launches": 0,
+    }
+
+
+def main():
+    args = parse()
+    dist = Dist()
+    try:
+        if args.impl == "reference":
+            if dist.rank == 0:
+                print(json.dumps(run_reference(args, dist)), flush=True)
+            return
+        line = run_ours(args, dist)
+        if dist.rank == 0:
+            print(json.dumps(line), flush=True)
+    finally:
+        dist.close()
+
+
+if __name__ == "__main__":
+    main()

@@ -1,0 +1,204 @@
+/*
+ * emin.h -- C ABI of the GB300 energy-minimisation prolongation library.
+ *
+ * The library minimises the energy tr(P^T A P) of an AMG prolongation P on a
+ * fixed sparsity pattern subject to the near-kernel constraint P B_c = B
+ * (Eqs. (trace), (inKern), (Constr) of Janna, Franceschini, Schroder and
+ * Olson, "Parallel Energy-Minimization Prolongation for Algebraic
+ * Multigrid"), with the restricted Jacobi-preconditioned conjugate gradient
+ * of Algorithm 3 after the set-up of Algorithm 2.  Every row of P is free
+ * (f = 0 in Eq. (11blk)); the paper's classical form P = [W; I] is the
+ * special case in which some rows are fixed.
+ *
+ * Conventions shared by every call:
+ *   - Indices are 32-bit signed ints; sparse matrices are CSR with row
+ *     pointers of length nrows+1 starting at 0 and column indices sorted
+ *     strictly ascending within each row (no duplicates).
+ *   - Floating-point inputs and outputs are IEEE double.  Dense blocks are
+ *     row-major.  "Values on P's pattern" means an array of nnz(P) doubles
+ *     in CSR order of P.
+ *   - A pointer argument is a host pointer unless the call's `on_device` /
+ *     `inputs_on_device` flag is 1, in which case it is a device pointer of
+ *     the context's device.  The caller keeps ownership of its buffers; the
+ *     library keeps no caller pointer after a call returns.
+ *   - All device work is ordered on the stream given at creation.  Calls
+ *     that return host results (status, scalars, host outputs) synchronise
+ *     that stream before returning; emin_iterate synchronises once at its
+ *     end.
+ *   - Every call returns an emin_status.  Device-detected conditions
+ *     (breakdown, invalid input found on the device) are recorded in the
+ *     context, reported by the call that detects them and by later calls.
+ *     The library never calls exit, abort or __trap.  A context in an error
+ *     state can always be destroyed.
+ */
+#ifndef EMIN_H
+#define EMIN_H
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+typedef struct emin_ctx emin_ctx; /* opaque, owned by the library */
+
+typedef enum {
+    EMIN_OK = 0,
+    EMIN_ERR_ARG = -1,       /* invalid argument or unsupported size          */
+    EMIN_ERR_PATTERN = -2,   /* CSR row pointers / columns invalid, unsorted, */
+                             /* duplicated or out of range                    */
+    EMIN_ERR_RANK = -3,      /* m_i < k or Gram matrix of a row not SPD       */
+                             /* (strict rank policy)                          */
+    EMIN_ERR_DIAG = -4,      /* A(i,i) missing or not positive                */
+    EMIN_ERR_BREAKDOWN = -5, /* y^T K y <= 0 or a non-finite scalar in CG     */
+    EMIN_ERR_CUDA = -6,      /* a CUDA runtime call failed                    */
+    EMIN_ERR_NOMEM = -7,     /* device or pinned host allocation failed       */
+    EMIN_ERR_TIMEOUT = -8,   /* reserved: a bounded device wait gave up       */
+    EMIN_ERR_STATE = -9      /* call not valid in the context's state         */
+} emin_status;
+
+enum { EMIN_FP64 = 0,   /* every step in IEEE double                           */
+       EMIN_MIXED = 1   /* A, P and the masked products in float; Gram         */
+                        /* factorisation, trace/step reductions and the final  */
+                        /* constraint-restoring projection in double           */
+};
+enum { EMIN_JACOBI = 0 };                       /* M_1 of Section 3.4          */
+enum { EMIN_RANK_STRICT = 0, EMIN_RANK_PINV = 1 };
+
+typedef struct {
+    int precision;    /* EMIN_FP64 or EMIN_MIXED                               */
+    int precond;      /* EMIN_JACOBI                                           */
+    int rank_policy;  /* EMIN_RANK_STRICT: a rank-deficient row is an error;   */
+                      /* EMIN_RANK_PINV: pseudo-inverse of that row's Gram     */
+                      /* matrix (the SVD branch of Algorithm 2), counted in    */
+                      /* emin_stats                                            */
+    int checks;       /* reserved (0)                                          */
+    void *stream;     /* cudaStream_t; NULL = legacy default stream            */
+} emin_opts;
+
+/* Fill *opts with the defaults: FP64, Jacobi, strict rank, stream NULL. */
+void emin_default_opts(emin_opts *opts);
+
+/*
+ * Create a context for one minimisation problem and run the set-up
+ * (Algorithm 2 and the first line of Algorithm 3).
+ *   n, nc, k     rows of P (= order of A), columns of P, near-kernel vectors
+ *                (1 <= k <= 8).
+ *   A_*          n x n symmetric matrix in CSR (A_val: nnz(A) doubles); every
+ *                row must hold a positive diagonal entry.
+ *   P_rowptr, P_col  the fixed pattern of P (n x nc CSR); at most 1024 entries
+ *                per row.
+ *   P0_val       tentative prolongation on P's pattern (nnz(P) doubles); need
+ *                not satisfy the constraint: the set-up corrects each row by
+ *                the least-norm solution of Eq. (resEq).
+ *   B            n x k fine near-kernel block V_f (row i = v_i of Eq. (Constr)).
+ *   Bc           nc x k coarse block V_c; row i's local block is B_i = Bc(J_i,:).
+ *   opts         options (NULL = defaults).
+ *   inputs_on_device  1 if every input pointer is a device pointer.
+ * All inputs are copied into library-owned device memory.  The set-up
+ * validates the CSR arrays on the device, forms the Gram matrix
+ * G_i = B_i^T B_i of every row in double, factorises it (Cholesky; rank
+ * tolerance 1e-12 relative to max diag G_i), corrects P0, scales rows by
+ * 1/A(i,i) for the Jacobi preconditioner (Theorem 1) and forms the initial
+ * residual r = -Pi_B K p0.  On error *out is NULL and nothing is leaked.
+ */
+int emin_create(emin_ctx **out, int n, int nc, int k,
+                const int *A_rowptr, const int *A_col, const double *A_val,
+                const int *P_rowptr, const int *P_col, const double *P0_val,
+                const double *B, const double *Bc,
+                const emin_opts *opts, int inputs_on_device);
+
+/*
+ * Replace values without changing the patterns, then restart the
+ * minimisation from the (new) P0 as emin_create does.  Any of A_val, B,
+ * P0_val may be NULL to keep the stored array.  Device or host per
+ * `on_device`.
+ */
+int emin_set_values(emin_ctx *ctx, const double *A_val, const double *B,
+                    const double *P0_val, int on_device);
+
+/* Restart the minimisation from the stored inputs (full set-up again). */
+int emin_reset(emin_ctx *ctx);
+
+/*
+ * Run up to n_iters iterations of Algorithm 3, resuming the state left by
+ * earlier calls.  tol is tau of Eq. (relRed): the iteration k whose energy
+ * decrease dE_k = gamma alpha (Eq. (CG_dEa)) satisfies dE_k < tau dE_1 is
+ * computed but not applied, and the minimisation is then converged (later
+ * calls do nothing); tol = 0 runs exactly n_iters steps unless the projected
+ * residual reaches rounding level (gamma <= f <K p0, M^{-1} K p0> with
+ * f = (100 eps)^2 of the working precision: 1e-28 in EMIN_FP64, 3.6e-11 in
+ * EMIN_MIXED), which also ends the minimisation.  *iters_done (may be NULL) receives the steps
+ * applied by this call; *rel_dE_last (may be NULL) the last dE_k / dE_1.
+ */
+int emin_iterate(emin_ctx *ctx, int n_iters, double tol, int *iters_done,
+                 double *rel_dE_last);
+
+/* Energy tr(P^T A P) = <P, mask_P(A P)> of the current P, in double. */
+int emin_energy(emin_ctx *ctx, double *E);
+
+/*
+ * Current prolongation P = P0 + dW on P's pattern (nnz(P) doubles).  In
+ * EMIN_MIXED the float correction is promoted to double and every row is
+ * projected back onto its constraint in double (least-norm correction as in
+ * Algorithm 2).
+ */
+int emin_get_p(emin_ctx *ctx, double *P_val_out, int out_on_device);
+
+/*
+ * Fixed-pattern product out = [Pi_B] mask_P(A X) (Section 4; Pi_B applied
+ * when `project` is 1) for X on P's pattern, computed by the same kernel as
+ * the iteration in the context's precision.
+ */
+int emin_kprod(emin_ctx *ctx, const double *X, double *out, int project, int on_device);
+
+/* out = mask_A(U V^T): for every stored (a, b) of A, sum_c U(a,c) V(b,c),
+ * U and V on P's pattern; out has nnz(A) doubles.  Double precision. */
+int emin_outer(emin_ctx *ctx, const double *U, const double *V, double *out, int on_device);
+
+/*
+ * Implicit adjoint of the converged minimiser P* (not in the paper; derived
+ * from the saddle-point system (sadsys)).  Given dL/dP on P's pattern it
+ * solves Pi K Pi u = 1/2 Pi dL/dP by the same restricted PCG (in double,
+ * from u = 0, at most max_adj_iters steps, tau = adj_tol) and returns
+ *   dL_dAval  nnz(A): -2 mask_A(U P^T), the part of dL/dA through P*;
+ *   dL_dB     n x k:  mu_i = G_i^{-1} B_i^T (dL/dP - 2 mask_P(A U))_i.
+ * The explicit dependence of L on A is the caller's to add.  The current P
+ * is taken as P*; only P (not the CG iterates) is kept from the forward.
+ * Either output may be NULL.  *adj_iters (may be NULL) receives the steps.
+ */
+int emin_backward(emin_ctx *ctx, const double *dL_dP, double *dL_dAval, double *dL_dB,
+                  int max_adj_iters, double adj_tol, int on_device, int *adj_iters);
+
+/*
+ * Statistics: dE_k of the computed iterations since the last (re)start
+ * (up to cap values into dE_hist, may be NULL), their count, the number of
+ * rank-deficient rows handled by EMIN_RANK_PINV, and the applied steps.
+ */
+int emin_stats(emin_ctx *ctx, double *dE_hist, int cap, int *n_hist,
+               int *n_rank_deficient, int *n_applied);
+
+/*
+ * Instrumentation.  emin_set_timing(ctx, 1) makes every later emin_iterate
+ * bracket each kernel launch of the iteration with CUDA events on the
+ * context's stream; emin_timing returns, per kernel class (0: masked product
+ * with projection, 1: direction update, 2: vector update), the summed event
+ * time in ms and the number of launches since timing was enabled (either
+ * array may be NULL; each has 3 entries), and in *total_launches the number
+ * of kernels the library launched since the context was created.
+ * Enabling (again) clears the sums.
+ */
+int emin_set_timing(emin_ctx *ctx, int enable);
+int emin_timing(emin_ctx *ctx, double *ms, long long *launches, long long *total_launches);
+
+/* Sizes of the context: nnz(A), nnz(P) (either may be NULL). */
+int emin_sizes(emin_ctx *ctx, long long *nnz_a, long long *nnz_p);
+
+/* Static description of a status code. */
+const char *emin_strerror(int status);
+
+/* Release every resource of the context (NULL is accepted). */
+void emin_destroy(emin_ctx *ctx);
+
+#ifdef __cplusplus
+}
+#endif
+#endif /* EMIN_H */

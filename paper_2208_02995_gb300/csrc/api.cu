@@ -1,0 +1,632 @@
+// Host side of libemin: the C ABI of include/emin.h.  Owns every device
+// buffer, validates inputs, sequences the set-up (Algorithm 2), the
+// restricted PCG iterations (Algorithm 3), the final prolongation and the
+// implicit adjoint.  All device work runs on the context's stream.
+#include <cuda_runtime.h>
+
+#include <atomic>
+#include <cstdio>
+#include <cstring>
+#include <new>
+#include <vector>
+
+#include "emin_internal.cuh"
+
+using namespace emin;
+
+struct emin_ctx {
+    int n = 0, nc = 0, k = 0;
+    long long nnz_a = 0, nnz_p = 0;
+    emin_opts opts{};
+    cudaStream_t stream = nullptr;
+    int device = 0;
+    Launch L{};
+    int maxrow_p = 0;
+    int lanes = 1;
+    int ndef = 0;
+    int sticky = EMIN_OK;  // device-detected error, reported by every later call
+    // inputs (library-owned copies)
+    int *Ap = nullptr, *Aj = nullptr, *Pp = nullptr, *Pj = nullptr;
+    double *Av = nullptr, *P0_in = nullptr, *P0 = nullptr, *B = nullptr, *Bc = nullptr;
+    float *Av32 = nullptr, *Bc32 = nullptr;
+    // set-up products
+    double *Ginv = nullptr, *dinv = nullptr;
+    float *Ginv32 = nullptr, *dinv32 = nullptr;
+    // restricted PCG workspaces
+    Work<double> w64;   // forward, EMIN_FP64
+    Work<float> w32;    // forward, EMIN_MIXED
+    Work<double> adj;   // adjoint (always double), allocated on first use
+    Work<double> aux;   // stand-alone reductions (energy)
+    // scratch
+    double *t64a = nullptr, *t64b = nullptr, *tA = nullptr, *tmu = nullptr;
+    float *t32a = nullptr, *t32b = nullptr;
+    int *dint = nullptr;       // [0] flags, [1] longest row of P, [2] rank-deficient rows
+    DevState *hstate = nullptr;  // pinned mirror
+    int *hint = nullptr;         // pinned mirror of dint
+    int applied_seen = 0;
+    std::vector<void *> dev_allocs;
+    // instrumentation
+    bool timing = false;
+    std::vector<cudaEvent_t> events;  // start/stop pairs, one per timed launch
+    double tms[3] = {0, 0, 0};
+    long long tlaunch[3] = {0, 0, 0};
+    long long launches_at_create = 0;
+};
+
+namespace emin {
+static std::atomic<long long> g_launches{0};
+void note_launch() { g_launches.fetch_add(1, std::memory_order_relaxed); }
+long long launches_so_far() { return g_launches.load(std::memory_order_relaxed); }
+}  // namespace emin
+
+namespace {
+
+struct DeviceGuard {
+    int prev = -1;
+    explicit DeviceGuard(int dev) {
+        if (cudaGetDevice(&prev) != cudaSuccess) prev = -1;
+        if (prev != dev) cudaSetDevice(dev);
+    }
+    ~DeviceGuard() {
+        int cur;
+        if (prev >= 0 && cudaGetDevice(&cur) == cudaSuccess && cur != prev) cudaSetDevice(prev);
+    }
+};
+
+template <class T>
+int dalloc(emin_ctx *c, T **p, long long count) {
+    size_t bytes = (size_t)(count > 0 ? count : 1) * sizeof(T);
+    bytes = (bytes + 255) & ~(size_t)255;
+    void *q = nullptr;
+    if (cudaMalloc(&q, bytes) != cudaSuccess) {
+        cudaGetLastError();
+        return EMIN_ERR_NOMEM;
+    }
+    c->dev_allocs.push_back(q);
+    *p = static_cast<T *>(q);
+    return EMIN_OK;
+}
+
+int cuda_status(cudaError_t e) {
+    if (e == cudaSuccess) return EMIN_OK;
+    cudaGetLastError();
+    return e == cudaErrorMemoryAllocation ? EMIN_ERR_NOMEM : EMIN_ERR_CUDA;
+}
+
+int check_launch() { return cuda_status(cudaGetLastError()); }
+
+#define EMIN_TRY(expr)                   \
+    do {                                 \
+        int _s = (expr);                 \
+        if (_s != EMIN_OK) return _s;    \
+    } while (0)
+
+int copy_in(emin_ctx *c, void *dst, const void *src, size_t bytes, int on_device) {
+    if (bytes == 0) return EMIN_OK;
+    if (!src) return EMIN_ERR_ARG;
+    return cuda_status(cudaMemcpyAsync(dst, src, bytes,
+                                       on_device ? cudaMemcpyDeviceToDevice : cudaMemcpyHostToDevice,
+                                       c->stream));
+}
+
+int copy_out(emin_ctx *c, void *dst, const void *src, size_t bytes, int on_device) {
+    if (bytes == 0) return EMIN_OK;
+    if (!dst) return EMIN_ERR_ARG;
+    return cuda_status(cudaMemcpyAsync(dst, src, bytes,
+                                       on_device ? cudaMemcpyDeviceToDevice : cudaMemcpyDeviceToHost,
+                                       c->stream));
+}
+
+int sync(emin_ctx *c) { return cuda_status(cudaStreamSynchronize(c->stream)); }
+
+Ops<double> ops64(const emin_ctx *c) {
+    return Ops<double>{c->n, c->nc, c->k, c->Ap, c->Aj, c->Av, c->Pp, c->Pj,
+                       c->Bc, c->Ginv, c->dinv, c->maxrow_p, c->lanes};
+}
+
+Ops<float> ops32(const emin_ctx *c) {
+    return Ops<float>{c->n, c->nc, c->k, c->Ap, c->Aj, c->Av32, c->Pp, c->Pj,
+                      c->Bc32, c->Ginv32, c->dinv32, c->maxrow_p, c->lanes};
+}
+
+template <class T>
+int alloc_work(emin_ctx *c, Work<T> &w, bool vectors) {
+    if (vectors) {
+        EMIN_TRY(dalloc(c, &w.R, c->nnz_p));
+        EMIN_TRY(dalloc(c, &w.Y, c->nnz_p));
+        EMIN_TRY(dalloc(c, &w.Yb, c->nnz_p));
+        EMIN_TRY(dalloc(c, &w.X, c->nnz_p));
+    }
+    EMIN_TRY(dalloc(c, &w.st, 1));
+    EMIN_TRY(dalloc(c, &w.partials, kMaxGrid));
+    w.hist_cap = 4096;
+    EMIN_TRY(dalloc(c, &w.hist, w.hist_cap));
+    EMIN_TRY(cuda_status(cudaMemsetAsync(w.st, 0, sizeof(DevState), c->stream)));
+    return EMIN_OK;
+}
+
+// r = -Pi_B K x0 in the workspace, with the convergence floor and gamma_0.
+// (Algorithm 3, first line, f = 0.)  For the adjoint the caller fills R.
+template <class T>
+int start_pcg(emin_ctx *c, const Ops<T> &o, Work<T> &w, const T *x0) {
+    launch_state_reset(c->L, w.st);
+    if (c->nnz_p > 0) {
+        EMIN_TRY(cuda_status(cudaMemsetAsync(w.Y, 0, sizeof(T) * c->nnz_p, c->stream)));
+        EMIN_TRY(cuda_status(cudaMemsetAsync(w.X, 0, sizeof(T) * c->nnz_p, c->stream)));
+    }
+    if (x0) launch_kprod<T>(c->L, o, x0, w.R, 0, DOT_NONE, w, 0);
+    launch_update<T>(c->L, o, w, UPD_FLOOR);
+    launch_project<T>(c->L, o, w.R, x0 ? T(-1) : T(1));
+    launch_update<T>(c->L, o, w, UPD_INIT);
+    return check_launch();
+}
+
+// Algorithm 2 plus the start of Algorithm 3 from the stored inputs.
+int run_setup(emin_ctx *c) {
+    const Launch &L = c->L;
+    EMIN_TRY(cuda_status(cudaMemsetAsync(c->dint, 0, 3 * sizeof(int), c->stream)));
+    launch_diag(L, c->n, c->Ap, c->Aj, c->Av, c->dinv, c->dinv32, c->dint);
+    launch_gram(L, c->n, c->k, c->Pp, c->Pj, c->Bc, c->Ginv, c->Ginv32, c->opts.rank_policy,
+                c->dint, c->dint + 2);
+    launch_restore(L, c->n, c->k, c->Pp, c->Pj, c->Bc, c->B, c->Ginv, c->P0_in, nullptr, nullptr,
+                   c->P0);
+    if (c->opts.precision == EMIN_MIXED) {
+        launch_to_float(L, c->Av, c->Av32, c->nnz_a);
+        launch_to_float(L, c->Bc, c->Bc32, (long long)c->nc * c->k);
+        launch_to_float(L, c->P0, c->t32a, c->nnz_p);
+        EMIN_TRY(start_pcg<float>(c, ops32(c), c->w32, c->t32a));
+    } else {
+        EMIN_TRY(start_pcg<double>(c, ops64(c), c->w64, c->P0));
+    }
+    c->applied_seen = 0;
+    return check_launch();
+}
+
+int read_flags(emin_ctx *c) {
+    EMIN_TRY(cuda_status(cudaMemcpyAsync(c->hint, c->dint, 3 * sizeof(int), cudaMemcpyDeviceToHost,
+                                         c->stream)));
+    EMIN_TRY(sync(c));
+    const int f = c->hint[0];
+    c->ndef = c->hint[2];
+    if (f & (F_ROWPTR | F_COL | F_ORDER)) return EMIN_ERR_PATTERN;
+    if (f & F_NONFINITE) return EMIN_ERR_ARG;
+    if (f & F_DIAG) return EMIN_ERR_DIAG;
+    if (f & F_RANK) return EMIN_ERR_RANK;
+    return EMIN_OK;
+}
+
+int read_state(emin_ctx *c, const DevState *st) {
+    EMIN_TRY(cuda_status(
+        cudaMemcpyAsync(c->hstate, st, sizeof(DevState), cudaMemcpyDeviceToHost, c->stream)));
+    return sync(c);
+}
+
+// current P on P's pattern, in double, into dst (device)
+int form_p(emin_ctx *c, double *dst) {
+    if (c->opts.precision == EMIN_MIXED) {
+        // promote the float correction and restore every row's constraint in double
+        launch_restore(c->L, c->n, c->k, c->Pp, c->Pj, c->Bc, c->B, c->Ginv, c->P0, nullptr,
+                       c->w32.X, dst);
+    } else if (c->nnz_p > 0) {
+        EMIN_TRY(cuda_status(cudaMemcpyAsync(dst, c->P0, sizeof(double) * c->nnz_p,
+                                             cudaMemcpyDeviceToDevice, c->stream)));
+        launch_axpby(c->L, c->nnz_p, 1.0, c->w64.X, 1.0, dst);
+    }
+    return check_launch();
+}
+
+int create_impl(emin_ctx *c, const int *A_rowptr, const int *A_col, const double *A_val,
+                const int *P_rowptr, const int *P_col, const double *P0_val, const double *B,
+                const double *Bc, int on_dev) {
+    const int n = c->n;
+    // sizes from the row pointers
+    int ends[4] = {0, 0, 0, 0};
+    if (on_dev) {
+        EMIN_TRY(cuda_status(cudaMemcpy(&ends[0], A_rowptr, sizeof(int), cudaMemcpyDeviceToHost)));
+        EMIN_TRY(cuda_status(cudaMemcpy(&ends[1], A_rowptr + n, sizeof(int), cudaMemcpyDeviceToHost)));
+        EMIN_TRY(cuda_status(cudaMemcpy(&ends[2], P_rowptr, sizeof(int), cudaMemcpyDeviceToHost)));
+        EMIN_TRY(cuda_status(cudaMemcpy(&ends[3], P_rowptr + n, sizeof(int), cudaMemcpyDeviceToHost)));
+    } else {
+        ends[0] = A_rowptr[0];
+        ends[1] = A_rowptr[n];
+        ends[2] = P_rowptr[0];
+        ends[3] = P_rowptr[n];
+    }
+    if (ends[0] != 0 || ends[2] != 0 || ends[1] < 0 || ends[3] < 0) return EMIN_ERR_PATTERN;
+    c->nnz_a = ends[1];
+    c->nnz_p = ends[3];
+    const long long nk = (long long)n * c->k, nck = (long long)c->nc * c->k;
+    const long long kk = (long long)n * (c->k * (c->k + 1) / 2);
+
+    EMIN_TRY(dalloc(c, &c->Ap, n + 1));
+    EMIN_TRY(dalloc(c, &c->Aj, c->nnz_a));
+    EMIN_TRY(dalloc(c, &c->Av, c->nnz_a));
+    EMIN_TRY(dalloc(c, &c->Pp, n + 1));
+    EMIN_TRY(dalloc(c, &c->Pj, c->nnz_p));
+    EMIN_TRY(dalloc(c, &c->P0_in, c->nnz_p));
+    EMIN_TRY(dalloc(c, &c->P0, c->nnz_p));
+    EMIN_TRY(dalloc(c, &c->B, nk));
+    EMIN_TRY(dalloc(c, &c->Bc, nck));
+    EMIN_TRY(dalloc(c, &c->Ginv, kk));
+    EMIN_TRY(dalloc(c, &c->Ginv32, kk));
+    EMIN_TRY(dalloc(c, &c->dinv, n));
+    EMIN_TRY(dalloc(c, &c->dinv32, n));
+    EMIN_TRY(dalloc(c, &c->dint, 4));
+    EMIN_TRY(dalloc(c, &c->t64a, c->nnz_p));
+    EMIN_TRY(dalloc(c, &c->t64b, c->nnz_p));
+    if (c->opts.precision == EMIN_MIXED) {
+        EMIN_TRY(dalloc(c, &c->Av32, c->nnz_a));
+        EMIN_TRY(dalloc(c, &c->Bc32, nck));
+        EMIN_TRY(dalloc(c, &c->t32a, c->nnz_p));
+        EMIN_TRY(dalloc(c, &c->t32b, c->nnz_p));
+        EMIN_TRY(alloc_work(c, c->w32, true));
+    } else {
+        EMIN_TRY(alloc_work(c, c->w64, true));
+    }
+    EMIN_TRY(alloc_work(c, c->aux, false));
+    if (cudaMallocHost((void **)&c->hstate, sizeof(DevState)) != cudaSuccess ||
+        cudaMallocHost((void **)&c->hint, 4 * sizeof(int)) != cudaSuccess) {
+        cudaGetLastError();
+        return EMIN_ERR_NOMEM;
+    }
+
+    EMIN_TRY(copy_in(c, c->Ap, A_rowptr, sizeof(int) * (n + 1), on_dev));
+    EMIN_TRY(copy_in(c, c->Aj, A_col, sizeof(int) * c->nnz_a, on_dev));
+    EMIN_TRY(copy_in(c, c->Av, A_val, sizeof(double) * c->nnz_a, on_dev));
+    EMIN_TRY(copy_in(c, c->Pp, P_rowptr, sizeof(int) * (n + 1), on_dev));
+    EMIN_TRY(copy_in(c, c->Pj, P_col, sizeof(int) * c->nnz_p, on_dev));
+    EMIN_TRY(copy_in(c, c->P0_in, P0_val, sizeof(double) * c->nnz_p, on_dev));
+    EMIN_TRY(copy_in(c, c->B, B, sizeof(double) * nk, on_dev));
+    EMIN_TRY(copy_in(c, c->Bc, Bc, sizeof(double) * nck, on_dev));
+
+    // validate on the device before any kernel indexes through the arrays
+    EMIN_TRY(cuda_status(cudaMemsetAsync(c->dint, 0, 4 * sizeof(int), c->stream)));
+    launch_validate_csr(c->L, n, n, c->Ap, (int)c->nnz_a, c->Aj, c->dint, c->dint + 3);
+    launch_validate_csr(c->L, n, c->nc, c->Pp, (int)c->nnz_p, c->Pj, c->dint, c->dint + 1);
+    launch_check_finite(c->L, c->Av, c->nnz_a, c->dint);
+    launch_check_finite(c->L, c->P0_in, c->nnz_p, c->dint);
+    launch_check_finite(c->L, c->B, nk, c->dint);
+    launch_check_finite(c->L, c->Bc, nck, c->dint);
+    EMIN_TRY(check_launch());
+    EMIN_TRY(cuda_status(cudaMemcpyAsync(c->hint, c->dint, 4 * sizeof(int), cudaMemcpyDeviceToHost,
+                                         c->stream)));
+    EMIN_TRY(sync(c));
+    const int f = c->hint[0];
+    if (f & (F_ROWPTR | F_COL | F_ORDER)) return EMIN_ERR_PATTERN;
+    if (f & F_NONFINITE) return EMIN_ERR_ARG;
+    c->maxrow_p = c->hint[1];
+    if (c->maxrow_p > kMaxRowP) return EMIN_ERR_ARG;
+    c->lanes = (c->maxrow_p <= 8) ? 1 : 32;
+
+    EMIN_TRY(run_setup(c));
+    return read_flags(c);
+}
+
+template <class T>
+int iterate_impl(emin_ctx *c, const Ops<T> &o, Work<T> &w, int n_iters, double tol,
+                 bool timed = false) {
+    launch_state_begin(c->L, w.st, tol);
+    timed = timed && c->timing && o.n > 0;
+    if (timed) {
+        const size_t need = (size_t)n_iters * 6;
+        while (c->events.size() < need) {
+            cudaEvent_t e;
+            if (cudaEventCreate(&e) != cudaSuccess) return cuda_status(cudaGetLastError());
+            c->events.push_back(e);
+        }
+    }
+    for (int it = 0; it < n_iters; ++it) {
+        cudaEvent_t *ev = timed ? &c->events[(size_t)it * 6] : nullptr;
+        if (timed) cudaEventRecord(ev[2], c->stream);
+        launch_ydir<T>(c->L, o, w);
+        if (timed) { cudaEventRecord(ev[3], c->stream); cudaEventRecord(ev[0], c->stream); }
+        launch_kprod<T>(c->L, o, w.Y, w.Yb, 1, DOT_ALPHA, w, 1);
+        if (timed) { cudaEventRecord(ev[1], c->stream); cudaEventRecord(ev[4], c->stream); }
+        launch_update<T>(c->L, o, w, UPD_STEP);
+        if (timed) cudaEventRecord(ev[5], c->stream);
+    }
+    EMIN_TRY(check_launch());
+    EMIN_TRY(read_state(c, w.st));
+    if (timed) {
+        for (int it = 0; it < n_iters; ++it) {
+            cudaEvent_t *ev = &c->events[(size_t)it * 6];
+            for (int j = 0; j < 3; ++j) {
+                float ms = 0.f;
+                if (cudaEventElapsedTime(&ms, ev[2 * j], ev[2 * j + 1]) == cudaSuccess) {
+                    c->tms[j] += ms;
+                    c->tlaunch[j] += 1;
+                }
+            }
+        }
+        cudaGetLastError();
+    }
+    return EMIN_OK;
+}
+
+}  // namespace
+
+extern "C" {
+
+void emin_default_opts(emin_opts *opts) {
+    if (!opts) return;
+    opts->precision = EMIN_FP64;
+    opts->precond = EMIN_JACOBI;
+    opts->rank_policy = EMIN_RANK_STRICT;
+    opts->checks = 0;
+    opts->stream = nullptr;
+}
+
+const char *emin_strerror(int status) {
+    switch (status) {
+        case EMIN_OK: return "ok";
+        case EMIN_ERR_ARG: return "invalid argument or unsupported size";
+        case EMIN_ERR_PATTERN: return "invalid CSR pattern (row pointers, range, order or duplicates)";
+        case EMIN_ERR_RANK: return "rank-deficient row constraint (m_i < k or Gram matrix not SPD)";
+        case EMIN_ERR_DIAG: return "diagonal entry of A missing or not positive";
+        case EMIN_ERR_BREAKDOWN: return "conjugate gradient breakdown (y^T K y <= 0 or non-finite)";
+        case EMIN_ERR_CUDA: return "CUDA runtime error";
+        case EMIN_ERR_NOMEM: return "out of device or pinned host memory";
+        case EMIN_ERR_TIMEOUT: return "bounded device wait expired";
+        case EMIN_ERR_STATE: return "call not valid in the current state";
+        default: return "unknown status";
+    }
+}
+
+void emin_destroy(emin_ctx *c) {
+    if (!c) return;
+    {
+        DeviceGuard g(c->device);
+        cudaStreamSynchronize(c->stream);
+        for (void *p : c->dev_allocs) cudaFree(p);
+        for (cudaEvent_t e : c->events) cudaEventDestroy(e);
+        if (c->hstate) cudaFreeHost(c->hstate);
+        if (c->hint) cudaFreeHost(c->hint);
+        cudaGetLastError();
+    }
+    delete c;
+}
+
+int emin_create(emin_ctx **out, int n, int nc, int k, const int *A_rowptr, const int *A_col,
+                const double *A_val, const int *P_rowptr, const int *P_col, const double *P0_val,
+                const double *B, const double *Bc, const emin_opts *opts, int inputs_on_device) {
+    if (!out) return EMIN_ERR_ARG;
+    *out = nullptr;
+    if (n < 0 || nc < 0 || k < 1 || k > kMaxK || !A_rowptr || !P_rowptr) return EMIN_ERR_ARG;
+    emin_opts o;
+    emin_default_opts(&o);
+    if (opts) o = *opts;
+    if ((o.precision != EMIN_FP64 && o.precision != EMIN_MIXED) || o.precond != EMIN_JACOBI ||
+        (o.rank_policy != EMIN_RANK_STRICT && o.rank_policy != EMIN_RANK_PINV))
+        return EMIN_ERR_ARG;
+    emin_ctx *c = new (std::nothrow) emin_ctx();
+    if (!c) return EMIN_ERR_NOMEM;
+    c->n = n;
+    c->nc = nc;
+    c->k = k;
+    c->opts = o;
+    c->stream = static_cast<cudaStream_t>(o.stream);
+    if (cudaGetDevice(&c->device) != cudaSuccess) {
+        cudaGetLastError();
+        delete c;
+        return EMIN_ERR_CUDA;
+    }
+    int nsm = 0, occ_rows = 0, occ_warps = 0;
+    cudaDeviceGetAttribute(&nsm, cudaDevAttrMultiProcessorCount, c->device);
+    if (nsm <= 0) nsm = 1;
+    occ_rows = 8;   // 2048 resident threads per SM at 256 threads per block
+    occ_warps = 8;
+    c->L.stream = c->stream;
+    c->L.grid_rows = nsm * occ_rows;
+    c->L.grid_warps = nsm * occ_warps;
+    if (c->L.grid_rows > kMaxGrid) c->L.grid_rows = kMaxGrid;
+    if (c->L.grid_warps > kMaxGrid) c->L.grid_warps = kMaxGrid;
+    set_iter_attributes();
+    set_adjoint_attributes();
+    c->launches_at_create = launches_so_far();
+    int st = create_impl(c, A_rowptr, A_col, A_val, P_rowptr, P_col, P0_val, B, Bc,
+                         inputs_on_device);
+    if (st != EMIN_OK) {
+        emin_destroy(c);
+        return st;
+    }
+    *out = c;
+    return EMIN_OK;
+}
+
+int emin_reset(emin_ctx *c) {
+    if (!c) return EMIN_ERR_ARG;
+    DeviceGuard g(c->device);
+    if (c->sticky == EMIN_ERR_CUDA) return c->sticky;
+    c->sticky = EMIN_OK;
+    return run_setup(c);
+}
+
+int emin_set_values(emin_ctx *c, const double *A_val, const double *B, const double *P0_val,
+                    int on_device) {
+    if (!c) return EMIN_ERR_ARG;
+    DeviceGuard g(c->device);
+    if (A_val) EMIN_TRY(copy_in(c, c->Av, A_val, sizeof(double) * c->nnz_a, on_device));
+    if (B) EMIN_TRY(copy_in(c, c->B, B, sizeof(double) * c->n * c->k, on_device));
+    if (P0_val) EMIN_TRY(copy_in(c, c->P0_in, P0_val, sizeof(double) * c->nnz_p, on_device));
+    EMIN_TRY(cuda_status(cudaMemsetAsync(c->dint, 0, 4 * sizeof(int), c->stream)));
+    launch_check_finite(c->L, c->Av, c->nnz_a, c->dint);
+    launch_check_finite(c->L, c->P0_in, c->nnz_p, c->dint);
+    launch_check_finite(c->L, c->B, (long long)c->n * c->k, c->dint);
+    EMIN_TRY(cuda_status(cudaMemcpyAsync(c->hint, c->dint, sizeof(int), cudaMemcpyDeviceToHost,
+                                         c->stream)));
+    EMIN_TRY(sync(c));
+    if (c->hint[0] & F_NONFINITE) return EMIN_ERR_ARG;
+    c->sticky = EMIN_OK;
+    EMIN_TRY(run_setup(c));
+    return read_flags(c);
+}
+
+int emin_iterate(emin_ctx *c, int n_iters, double tol, int *iters_done, double *rel_dE_last) {
+    if (!c || n_iters < 0 || !(tol >= 0)) return EMIN_ERR_ARG;
+    DeviceGuard g(c->device);
+    if (iters_done) *iters_done = 0;
+    if (c->sticky != EMIN_OK) return c->sticky;
+    int s;
+    const DevState *hs = c->hstate;
+    if (c->opts.precision == EMIN_MIXED)
+        s = iterate_impl<float>(c, ops32(c), c->w32, n_iters, tol, true);
+    else
+        s = iterate_impl<double>(c, ops64(c), c->w64, n_iters, tol, true);
+    if (s != EMIN_OK) {
+        c->sticky = s;
+        return s;
+    }
+    if (iters_done) *iters_done = hs->applied - c->applied_seen;
+    c->applied_seen = hs->applied;
+    if (rel_dE_last) *rel_dE_last = (hs->k > 0 && hs->dE1 != 0.0) ? hs->dE_last / hs->dE1 : 0.0;
+    if (hs->status != EMIN_OK) {
+        c->sticky = hs->status;
+        return hs->status;
+    }
+    return EMIN_OK;
+}
+
+int emin_get_p(emin_ctx *c, double *P_out, int out_on_device) {
+    if (!c) return EMIN_ERR_ARG;
+    DeviceGuard g(c->device);
+    if (c->sticky != EMIN_OK) return c->sticky;
+    EMIN_TRY(form_p(c, c->t64a));
+    EMIN_TRY(copy_out(c, P_out, c->t64a, sizeof(double) * c->nnz_p, out_on_device));
+    return sync(c);
+}
+
+int emin_energy(emin_ctx *c, double *E) {
+    if (!c || !E) return EMIN_ERR_ARG;
+    DeviceGuard g(c->device);
+    if (c->sticky != EMIN_OK) return c->sticky;
+    EMIN_TRY(form_p(c, c->t64a));
+    launch_state_reset(c->L, c->aux.st);
+    launch_kprod<double>(c->L, ops64(c), c->t64a, c->t64b, 0, DOT_AUX, c->aux, 0);
+    EMIN_TRY(check_launch());
+    EMIN_TRY(read_state(c, c->aux.st));
+    *E = c->hstate->aux;
+    return EMIN_OK;
+}
+
+int emin_kprod(emin_ctx *c, const double *X, double *out, int project, int on_device) {
+    if (!c) return EMIN_ERR_ARG;
+    DeviceGuard g(c->device);
+    EMIN_TRY(copy_in(c, c->t64a, X, sizeof(double) * c->nnz_p, on_device));
+    if (c->opts.precision == EMIN_MIXED) {
+        launch_to_float(c->L, c->t64a, c->t32a, c->nnz_p);
+        launch_kprod<float>(c->L, ops32(c), c->t32a, c->t32b, project ? 1 : 0, DOT_NONE, c->w32, 0);
+        launch_to_double(c->L, c->t32b, c->t64b, c->nnz_p);
+    } else {
+        launch_kprod<double>(c->L, ops64(c), c->t64a, c->t64b, project ? 1 : 0, DOT_NONE, c->aux, 0);
+    }
+    EMIN_TRY(check_launch());
+    EMIN_TRY(copy_out(c, out, c->t64b, sizeof(double) * c->nnz_p, on_device));
+    return sync(c);
+}
+
+int emin_outer(emin_ctx *c, const double *U, const double *V, double *out, int on_device) {
+    if (!c) return EMIN_ERR_ARG;
+    DeviceGuard g(c->device);
+    if (!c->tA) EMIN_TRY(dalloc(c, &c->tA, c->nnz_a));
+    EMIN_TRY(copy_in(c, c->t64a, U, sizeof(double) * c->nnz_p, on_device));
+    EMIN_TRY(copy_in(c, c->t64b, V, sizeof(double) * c->nnz_p, on_device));
+    launch_outer(c->L, c->n, c->Ap, c->Aj, c->Pp, c->Pj, c->t64a, c->t64b, 1.0, c->tA, c->maxrow_p);
+    EMIN_TRY(check_launch());
+    EMIN_TRY(copy_out(c, out, c->tA, sizeof(double) * c->nnz_a, on_device));
+    return sync(c);
+}
+
+int emin_backward(emin_ctx *c, const double *dL_dP, double *dL_dAval, double *dL_dB,
+                  int max_adj_iters, double adj_tol, int on_device, int *adj_iters) {
+    if (!c || !dL_dP || max_adj_iters < 0 || !(adj_tol >= 0)) return EMIN_ERR_ARG;
+    DeviceGuard g(c->device);
+    if (c->sticky != EMIN_OK) return c->sticky;
+    if (!c->adj.R) {
+        EMIN_TRY(alloc_work(c, c->adj, true));
+        if (!c->tA) EMIN_TRY(dalloc(c, &c->tA, c->nnz_a));
+        EMIN_TRY(dalloc(c, &c->tmu, (long long)c->n * c->k));
+    }
+    const Ops<double> o = ops64(c);
+    Work<double> &w = c->adj;
+    // P* (kept from the forward) and dL/dP
+    EMIN_TRY(form_p(c, c->t64a));
+    EMIN_TRY(copy_in(c, c->t64b, dL_dP, sizeof(double) * c->nnz_p, on_device));
+    // Pi K Pi u = 1/2 Pi dL/dP from u = 0
+    if (c->nnz_p > 0) {
+        EMIN_TRY(cuda_status(cudaMemcpyAsync(w.R, c->t64b, sizeof(double) * c->nnz_p,
+                                             cudaMemcpyDeviceToDevice, c->stream)));
+        launch_axpby(c->L, c->nnz_p, 0.0, c->t64b, 0.5, w.R);
+    }
+    EMIN_TRY(start_pcg<double>(c, o, w, nullptr));
+    EMIN_TRY(iterate_impl<double>(c, o, w, max_adj_iters, adj_tol));
+    if (c->hstate->status != EMIN_OK) return c->hstate->status;
+    if (adj_iters) *adj_iters = c->hstate->applied;
+    // S = mask(A U);  x = dL/dP - 2 S;  mu = G^{-1} B_i^T x
+    launch_kprod<double>(c->L, o, w.X, w.Yb, 0, DOT_NONE, w, 0);
+    launch_axpby(c->L, c->nnz_p, 1.0, c->t64b, -2.0, w.Yb);
+    if (dL_dB) {
+        launch_lsq(c->L, c->n, c->k, c->Pp, c->Pj, c->Bc, c->Ginv, w.Yb, c->tmu);
+        EMIN_TRY(check_launch());
+        EMIN_TRY(copy_out(c, dL_dB, c->tmu, sizeof(double) * c->n * c->k, on_device));
+    }
+    if (dL_dAval) {
+        launch_outer(c->L, c->n, c->Ap, c->Aj, c->Pp, c->Pj, w.X, c->t64a, -2.0, c->tA, c->maxrow_p);
+        EMIN_TRY(check_launch());
+        EMIN_TRY(copy_out(c, dL_dAval, c->tA, sizeof(double) * c->nnz_a, on_device));
+    }
+    return sync(c);
+}
+
+int emin_stats(emin_ctx *c, double *dE_hist, int cap, int *n_hist, int *n_rank_deficient,
+               int *n_applied) {
+    if (!c) return EMIN_ERR_ARG;
+    DeviceGuard g(c->device);
+    const Work<double> *w64 = &c->w64;
+    const DevState *st = (c->opts.precision == EMIN_MIXED) ? c->w32.st : w64->st;
+    const double *hist = (c->opts.precision == EMIN_MIXED) ? c->w32.hist : w64->hist;
+    const int hcap = (c->opts.precision == EMIN_MIXED) ? c->w32.hist_cap : w64->hist_cap;
+    EMIN_TRY(read_state(c, st));
+    const int k = c->hstate->k;
+    if (n_hist) *n_hist = k;
+    if (n_applied) *n_applied = c->hstate->applied;
+    if (n_rank_deficient) *n_rank_deficient = c->ndef;
+    if (dE_hist && cap > 0) {
+        int m = k < cap ? k : cap;
+        if (m > hcap) m = hcap;
+        if (m > 0) {
+            EMIN_TRY(cuda_status(cudaMemcpyAsync(dE_hist, hist, sizeof(double) * m,
+                                                 cudaMemcpyDeviceToHost, c->stream)));
+            EMIN_TRY(sync(c));
+        }
+    }
+    return EMIN_OK;
+}
+
+int emin_set_timing(emin_ctx *c, int enable) {
+    if (!c) return EMIN_ERR_ARG;
+    c->timing = enable != 0;
+    for (int j = 0; j < 3; ++j) {
+        c->tms[j] = 0.0;
+        c->tlaunch[j] = 0;
+    }
+    return EMIN_OK;
+}
+
+int emin_timing(emin_ctx *c, double *ms, long long *launches, long long *total_launches) {
+    if (!c) return EMIN_ERR_ARG;
+    for (int j = 0; j < 3; ++j) {
+        if (ms) ms[j] = c->tms[j];
+        if (launches) launches[j] = c->tlaunch[j];
+    }
+    if (total_launches) *total_launches = launches_so_far() - c->launches_at_create;
+    return EMIN_OK;
+}
+
+int emin_sizes(emin_ctx *c, long long *nnz_a, long long *nnz_p) {
+    if (!c) return EMIN_ERR_ARG;
+    if (nnz_a) *nnz_a = c->nnz_a;
+    if (nnz_p) *nnz_p = c->nnz_p;
+    return EMIN_OK;
+}
+
+}  // extern "C"

@@ -1,0 +1,187 @@
+// Device helpers: typed fused multiply-add, compensated float accumulation
+// and deterministic block / grid reductions to double.
+#pragma once
+#include <cuda_runtime.h>
+
+#include "emin_internal.cuh"
+
+namespace emin {
+
+__device__ __forceinline__ double fmat(double a, double b, double c) { return fma(a, b, c); }
+__device__ __forceinline__ float fmat(float a, float b, float c) { return fmaf(a, b, c); }
+
+// ---------------------------------------------------------------------------
+// Dot-product accumulators.  Dot<double> is a plain FMA chain.  Dot<float>
+// keeps an unevaluated float pair (hi + lo): each product is split exactly
+// with an FMA (a*b = p + e) and added with Knuth's two-sum, so the float
+// products of the mixed path are summed to about 44 bits; the pair is
+// converted to double once per warp.  The _rn intrinsics keep the compiler
+// from contracting the error terms into FMAs.
+// ---------------------------------------------------------------------------
+template <class T>
+struct Dot;
+
+template <>
+struct Dot<double> {
+    double v = 0.0;
+    __device__ __forceinline__ void add(double a, double b) { v = fma(a, b, v); }
+    __device__ __forceinline__ double warp_total() {
+        double s = v;
+#pragma unroll
+        for (int o = 16; o > 0; o >>= 1) s += __shfl_down_sync(0xffffffffu, s, o);
+        return s;  // lane 0 holds the warp sum
+    }
+};
+
+__device__ __forceinline__ void two_sum(float a, float b, float &s, float &e) {
+    s = __fadd_rn(a, b);
+    float v = __fsub_rn(s, a);
+    e = __fadd_rn(__fsub_rn(a, __fsub_rn(s, v)), __fsub_rn(b, v));
+}
+
+__device__ __forceinline__ void ff_add(float &hi, float &lo, float bhi, float blo) {
+    float s, e;
+    two_sum(hi, bhi, s, e);
+    e = __fadd_rn(e, __fadd_rn(lo, blo));
+    hi = __fadd_rn(s, e);
+    lo = __fsub_rn(e, __fsub_rn(hi, s));
+}
+
+template <>
+struct Dot<float> {
+    float hi = 0.f, lo = 0.f;
+    __device__ __forceinline__ void add(float a, float b) {
+        float p = __fmul_rn(a, b);
+        float pe = fmaf(a, b, -p);  // exact error of the product
+        ff_add(hi, lo, p, pe);
+    }
+    __device__ __forceinline__ double warp_total() {
+        float h = hi, l = lo;
+#pragma unroll
+        for (int o = 16; o > 0; o >>= 1) {
+            float oh = __shfl_down_sync(0xffffffffu, h, o);
+            float ol = __shfl_down_sync(0xffffffffu, l, o);
+            ff_add(h, l, oh, ol);
+        }
+        return (double)h + (double)l;
+    }
+};
+
+// Sum of one double per thread over the block, fixed order; result valid in
+// thread 0.  `sh` holds at least 32 doubles.
+__device__ __forceinline__ double block_sum(double v, double *sh) {
+    const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) v += __shfl_down_sync(0xffffffffu, v, o);
+    __syncthreads();
+    if (lane == 0) sh[w] = v;
+    __syncthreads();
+    double s = 0.0;
+    if (threadIdx.x == 0)
+        for (int i = 0; i < (int)(blockDim.x >> 5); ++i) s += sh[i];
+    return s;
+}
+
+// Deterministic grid reduction: every block passes its total (valid in
+// thread 0); the last block to arrive sums the block totals in block order.
+// Returns true in thread 0 of that last block, with *total set.
+__device__ __forceinline__ bool grid_reduce(double block_total, double *partials,
+                                            unsigned int *ticket, double *total) {
+    __shared__ bool am_last;
+    __shared__ double sh[32];
+    if (threadIdx.x == 0) {
+        partials[blockIdx.x] = block_total;
+        __threadfence();
+        unsigned int t = atomicAdd(ticket, 1u);
+        am_last = (t == gridDim.x - 1);
+    }
+    __syncthreads();
+    if (!am_last) return false;
+    __threadfence();
+    double s = 0.0;
+    for (int b = threadIdx.x; b < (int)gridDim.x; b += blockDim.x) s += __ldcg(partials + b);
+    s = block_sum(s, sh);
+    if (threadIdx.x == 0) {
+        *total = s;
+        *ticket = 0u;
+    }
+    return threadIdx.x == 0;
+}
+
+// Warp totals of a Dot accumulator gathered into one double per block.
+template <class T>
+__device__ __forceinline__ double block_dot_total(Dot<T> &d, double *sh) {
+    double wt = d.warp_total();
+    const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
+    __syncthreads();
+    if (lane == 0) sh[w] = wt;
+    __syncthreads();
+    double s = 0.0;
+    if (threadIdx.x == 0)
+        for (int i = 0; i < (int)(blockDim.x >> 5); ++i) s += sh[i];
+    return s;
+}
+
+// ---- scalar steps of Algorithm 3, run by one thread after a reduction ----
+
+// After y^T y_ is known: alpha, dE_k = gamma alpha (Eq. (CG_dEa)), the stop
+// test dE_k < tau dE_1 of Eq. (relRed) (the step is then not applied).
+__device__ __forceinline__ void finalize_alpha(DevState *st, double ydy, double *hist, int cap) {
+    st->ydy = ydy;
+    const double g = st->gamma;
+    if (!(ydy > 0.0) || !isfinite(ydy) || !isfinite(g)) {
+        st->stop = 2;
+        st->status = EMIN_ERR_BREAKDOWN;
+        return;
+    }
+    const double alpha = g / ydy;
+    const double dE = g * alpha;
+    const int kk = st->k;
+    st->k = kk + 1;
+    if (kk < cap) hist[kk] = dE;
+    if (kk == 0) st->dE1 = dE;
+    st->dE_last = dE;
+    st->alpha = alpha;
+    if (dE < st->tau * st->dE1) st->stop = 1;
+}
+
+// Convergence floor of gamma relative to the unprojected <b, M^{-1} b>:
+// (100 eps)^2 of the working precision (the residual cannot shrink further
+// than about 100 ulps relative to the right-hand side).
+template <class T>
+struct GammaFloor;
+template <>
+struct GammaFloor<double> {
+    static constexpr double value = kGammaFloor;  // (100 * 2^-53)^2 ~ 1.2e-28
+};
+template <>
+struct GammaFloor<float> {
+    static constexpr double value = 3.6e-11;      // (100 * 2^-24)^2 ~ 3.6e-11
+};
+
+// After the new gamma = r^T M^{-1} r is known.
+__device__ __forceinline__ void finalize_gamma(DevState *st, double gnew, int mode,
+                                               double floor_factor) {
+    if (mode == UPD_FLOOR) {
+        st->gamma_floor = floor_factor * gnew;
+        return;
+    }
+    if (!isfinite(gnew)) {
+        st->stop = 2;
+        st->status = EMIN_ERR_BREAKDOWN;
+        return;
+    }
+    if (mode == UPD_INIT) {
+        st->gamma = gnew;
+        st->gamma_old = 0.0;
+        st->beta = 0.0;
+    } else {
+        st->applied += 1;
+        st->beta = gnew / st->gamma;
+        st->gamma_old = st->gamma;
+        st->gamma = gnew;
+    }
+    if (!(gnew > st->gamma_floor)) st->stop = 1;
+}
+
+}  // namespace emin

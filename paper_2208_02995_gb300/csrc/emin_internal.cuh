@@ -1,0 +1,144 @@
+// Internal declarations shared by the CUDA translation units of libemin.
+//
+// Data layout in device memory (all arrays library-owned):
+//   A      CSR: rowptr int32[n+1], col int32[nnz(A)], val f64[nnz(A)]
+//          (+ f32 copy in mixed precision)
+//   P      CSR pattern: rowptr int32[n+1], col int32[nnz(P)]; every vector of
+//          the iteration (R, Y, Y_, dW, P0) is a value array on this pattern
+//   B      f64[n*k] row-major; Bc f64[nc*k] row-major (+ f32 copy)
+//   Ginv   per row, the inverse (or pseudo-inverse) of the Gram matrix
+//          G_i = B_i^T B_i, packed lower triangle, f64[n*k(k+1)/2] (+ f32)
+//   dinv   1/A(i,i), f64[n] and f32[n]
+#pragma once
+#include <cuda_runtime.h>
+
+#include <cstddef>
+#include <cstdint>
+
+#include "../../include/emin.h"
+
+namespace emin {
+
+constexpr int kMaxK = 8;           // near-kernel vectors per row
+constexpr int kMaxRowP = 1024;     // entries of a row of P (warp kernel staging)
+constexpr int kBlock = 256;        // threads per block of every kernel
+constexpr int kMaxGrid = 8192;     // blocks of a reducing kernel (partials buffer)
+constexpr double kRankTol = 1e-12; // pivot tolerance relative to max diag(G_i)
+constexpr double kGammaFloor = 1e-28;
+
+// device-side error flags (bit set) found while validating / setting up
+enum : int {
+    F_ROWPTR = 1,     // row pointers not monotone or out of range
+    F_COL = 2,        // a column index out of range
+    F_ORDER = 4,      // columns not strictly ascending in a row
+    F_DIAG = 8,       // A(i,i) missing, not positive or not finite
+    F_RANK = 16,      // rank-deficient Gram matrix (strict policy)
+    F_NONFINITE = 32, // non-finite value in A, B, Bc or P0
+    F_ROWLEN = 64,    // a row of P longer than kMaxRowP
+};
+
+// Scalars of one restricted PCG run (Algorithm 3), resident on the device.
+struct DevState {
+    double gamma;        // r^T z of the current residual
+    double gamma_old;
+    double alpha;        // gamma / y^T y_
+    double beta;         // gamma / gamma_old (0 before the first step)
+    double ydy;          // y^T y_
+    double dE1;          // dE of the first computed iteration
+    double dE_last;
+    double gamma_floor;  // convergence floor of gamma
+    double tau;          // tolerance of Eq. (relRed)
+    double aux;          // result of a stand-alone reduction (energy, ...)
+    int k;               // iterations computed since (re)start
+    int applied;         // steps applied since (re)start
+    int stop;            // 0 running, 1 converged, 2 error
+    int status;          // emin_status of a device-detected error
+    unsigned int ticket[4];
+};
+
+// reduction targets of the masked-product kernel
+enum DotMode : int { DOT_NONE = 0, DOT_ALPHA = 1, DOT_AUX = 2 };
+// modes of the update kernel
+enum UpdMode : int { UPD_INIT = 0, UPD_STEP = 1, UPD_FLOOR = 2 };
+
+// One restricted PCG workspace in value type T.
+template <class T>
+struct Work {
+    T *R = nullptr, *Y = nullptr, *Yb = nullptr, *X = nullptr;
+    DevState *st = nullptr;
+    double *partials = nullptr;
+    double *hist = nullptr;
+    int hist_cap = 0;
+};
+
+// Everything a kernel launch needs to know about the problem.
+template <class T>
+struct Ops {
+    int n, nc, k;
+    const int *Ap, *Aj;
+    const T *Av;
+    const int *Pp, *Pj;
+    const T *Bc;
+    const T *Ginv;
+    const T *dinv;
+    int maxrow;    // longest row of P
+    int lanes;     // lanes per row of the vector kernels (1 or 32)
+};
+
+struct Launch {
+    cudaStream_t stream;
+    int grid_rows;    // grid of thread-per-row kernels
+    int grid_warps;   // grid of warp-per-row kernels
+};
+
+// shared-memory slots per warp for a row of P: the longest row rounded up
+// to a multiple of 32 (at least 32, at most kMaxRowP)
+inline int staging_cap(int maxrow) {
+    int c = ((maxrow + 31) / 32) * 32;
+    if (c < 32) c = 32;
+    return c > kMaxRowP ? kMaxRowP : c;
+}
+
+// process-wide count of kernels launched by the library (instrumentation)
+void note_launch();
+long long launches_so_far();
+
+// ---- set-up kernels (setup_kernels.cu) ----
+void launch_validate_csr(const Launch &L, int nrows, int ncols, const int *rowptr, int nnz,
+                         const int *col, int *flags, int *maxrow);
+void launch_check_finite(const Launch &L, const double *v, long long count, int *flags);
+void launch_diag(const Launch &L, int n, const int *Ap, const int *Aj, const double *Av,
+                 double *dinv64, float *dinv32, int *flags);
+void launch_gram(const Launch &L, int n, int k, const int *Pp, const int *Pj, const double *Bc,
+                 double *Ginv, float *Ginv32, int policy, int *flags, int *ndef);
+void launch_restore(const Launch &L, int n, int k, const int *Pp, const int *Pj,
+                    const double *Bc, const double *B, const double *Ginv, const double *base,
+                    const double *add64, const float *add32, double *P);
+void launch_to_float(const Launch &L, const double *src, float *dst, long long count);
+void launch_to_double(const Launch &L, const float *src, double *dst, long long count);
+
+// ---- iteration kernels (iter_kernels.cu) ----
+template <class T>
+void launch_kprod(const Launch &L, const Ops<T> &o, const T *Y, T *out, int project,
+                  int dot_mode, Work<T> &w, int check_stop);
+template <class T>
+void launch_project(const Launch &L, const Ops<T> &o, T *x, T scale);
+template <class T>
+void launch_ydir(const Launch &L, const Ops<T> &o, Work<T> &w);
+template <class T>
+void launch_update(const Launch &L, const Ops<T> &o, Work<T> &w, int mode);
+void launch_state_reset(const Launch &L, DevState *st);
+void set_iter_attributes();
+void set_adjoint_attributes();
+void launch_state_begin(const Launch &L, DevState *st, double tau);
+
+// ---- adjoint kernels (adjoint_kernels.cu) ----
+void launch_outer(const Launch &L, int n, const int *Ap, const int *Aj, const int *Pp,
+                  const int *Pj, const double *U, const double *V, double scale, double *out,
+                  int maxrow);
+void launch_lsq(const Launch &L, int n, int k, const int *Pp, const int *Pj, const double *Bc,
+                const double *Ginv, const double *x, double *mu);
+void launch_axpby(const Launch &L, long long count, double a, const double *x, double b,
+                  double *y);
+
+}  // namespace emin

@@ -1,0 +1,287 @@
+"""Parity of the CUDA path (through the C ABI) with the FP64 CPU oracle.
+
+Bars: FP64 path within 1e-9 relative Frobenius of the oracle after a fixed
+iteration count (1e-12 relative for a single masked product); mixed path
+within 1e-5 relative energy with max |P B_c - B| <= 1e-12."""
+import numpy as np
+import pytest
+
+from oracle.oracle import Oracle
+from paper_2208_02995_gb300 import inputs as I
+
+pytestmark = pytest.mark.gpu
+
+FP64_TOL = 1e-9
+KPROD_TOL = 1e-12
+MIXED_E_TOL = 1e-5
+CONSTRAINT_TOL = 1e-12
+
+
+@pytest.fixture(scope="module", autouse=True)
+def _gpu():
+    import torch
+    if not torch.cuda.is_available():
+        pytest.skip("no CUDA device")
+    from paper_2208_02995_gb300 import build
+    build.build()
+
+
+def ctx(prob, precision="fp64", **kw):
+    from paper_2208_02995_gb300.emin import Context
+    return Context(prob, precision=precision, **kw)
+
+
+def relf(a, b):
+    return float(np.linalg.norm(a - b) / max(np.linalg.norm(b), 1e-300))
+
+
+SMALL = [
+    I.poisson2d(64, 2),                       # workload 1 at full size
+    I.diffusion3d_fv(21, 3),                  # ragged aggregates (21 = 7*3)
+    I.diffusion3d_fv(23, 3),                  # remainder aggregate 5 wide
+    I.aniso3d(14, 1e-3, 2),
+    I.elasticity3d(7, 0.3, 3),                # 6 rigid-body modes, rows up to 48
+    I.elasticity3d(8, 0.25, 3, 1.5, 5),
+    I.random_problem(300, 60, 1, seed=1, wide_rows=(3, 77), wide=40),
+    I.random_problem(200, 90, 3, p_per_row=7, seed=2, wide_rows=(5,), wide=80),
+    I.random_problem(150, 400, 2, p_per_row=5, seed=3, wide_rows=(9,), wide=300),
+]
+SMALL_IDS = [p.name for p in SMALL]
+
+
+@pytest.mark.parametrize("prob", SMALL, ids=SMALL_IDS)
+@pytest.mark.parametrize("precision", ["fp64", "mixed"])
+def test_kprod_matches_oracle(prob, precision):
+    o = Oracle(prob)
+    c = ctx(prob, precision)
+    X = np.random.default_rng(0).standard_normal(prob.nnz_p)
+    tol = KPROD_TOL if precision == "fp64" else 2e-6
+    for project in (False, True):
+        ref = o.kprod(X)
+        if project:
+            ref = o.project(ref)
+        got = c.kprod(X, project=project)
+        assert np.abs(got - ref).max() <= tol * np.abs(ref).max(), project
+
+
+@pytest.mark.parametrize("prob", SMALL, ids=SMALL_IDS)
+def test_setup_matches_oracle(prob):
+    o = Oracle(prob)
+    c = ctx(prob)
+    P = c.get_p()
+    assert np.abs(P - o.P0).max() <= 1e-13 * max(1.0, np.abs(o.P0).max())
+    assert o.constraint_error(P) <= CONSTRAINT_TOL
+    assert abs(c.energy() - o.energy(o.P0)) <= 1e-12 * abs(o.energy(o.P0))
+
+
+@pytest.mark.parametrize("prob", SMALL, ids=SMALL_IDS)
+def test_fp64_iterations_match_oracle(prob):
+    o = Oracle(prob)
+    its = 12
+    ref = o.minimize(its, 0.0)
+    c = ctx(prob)
+    done, _ = c.iterate(its, 0.0)
+    assert done == ref["applied"]
+    P = c.get_p()
+    assert relf(P, ref["P"]) <= FP64_TOL
+    st = c.stats()
+    # dE_k to 1e-9 relative, or to rounding level of dE_1 once dE_k is that small
+    assert np.allclose(st["dE"], ref["dE"], rtol=1e-9, atol=1e-13 * ref["dE"][0])
+    assert o.constraint_error(P) <= CONSTRAINT_TOL
+    assert abs(c.energy() - o.energy(ref["P"])) <= 1e-11 * abs(o.energy(ref["P"]))
+
+
+@pytest.mark.parametrize("prob", SMALL, ids=SMALL_IDS)
+def test_mixed_iterations_match_oracle(prob):
+    o = Oracle(prob)
+    its = 12
+    ref = o.minimize(its, 0.0)
+    c = ctx(prob, "mixed")
+    c.iterate(its, 0.0)
+    P = c.get_p()
+    E, Eref = c.energy(), o.energy(ref["P"])
+    assert abs(E - Eref) <= MIXED_E_TOL * abs(Eref)
+    assert o.constraint_error(P) <= CONSTRAINT_TOL
+    # P itself is only determined to float accuracy along flat energy
+    # directions; the error is reported, with a sanity bound here
+    assert relf(P, ref["P"]) <= 1e-2
+
+
+def test_resume_equals_single_call():
+    prob = I.diffusion3d_fv(16, 3)
+    a, b = ctx(prob), ctx(prob)
+    a.iterate(10)
+    b.iterate(4)
+    b.iterate(6)
+    assert np.array_equal(a.get_p(), b.get_p())
+    # reset restarts from P0 and reproduces the run bit for bit
+    P10 = a.get_p()
+    a.reset()
+    a.iterate(10)
+    assert np.array_equal(a.get_p(), P10)
+
+
+@pytest.mark.parametrize("tau", [0.3, 0.05])
+def test_energy_stop_test(tau):
+    prob = I.aniso3d(12, 1e-3, 2)
+    o = Oracle(prob)
+    ref = o.minimize(200, tau)
+    c = ctx(prob)
+    done, rel = c.iterate(200, tau)
+    assert done == ref["applied"]
+    assert len(c.stats()["dE"]) == len(ref["dE"])
+    assert rel < tau
+    assert relf(c.get_p(), ref["P"]) <= FP64_TOL
+    assert c.iterate(5, tau)[0] == 0  # converged: later calls do nothing
+
+
+def test_converges_to_oracle_limit():
+    prob = I.elasticity3d(5, 0.3, 2)
+    o = Oracle(prob)
+    ref = o.minimize(600, 0.0)
+    c = ctx(prob)
+    c.iterate(600, 0.0)
+    assert relf(c.get_p(), ref["P"]) <= 1e-9
+
+
+def test_no_freedom_keeps_p0():
+    prob = I.poisson2d(8, 2)
+    keep = prob.P0_val != 0
+    rows = np.repeat(np.arange(prob.n), np.diff(prob.P_rowptr))
+    Pp = np.zeros(prob.n + 1, dtype=np.int32)
+    np.cumsum(np.bincount(rows[keep], minlength=prob.n), out=Pp[1:])
+    p2 = I.Problem("p0pattern", prob.n, prob.nc, 1, prob.A_rowptr, prob.A_col, prob.A_val,
+                   Pp, prob.P_col[keep], prob.P0_val[keep], prob.B, prob.Bc)
+    c = ctx(p2)
+    done, _ = c.iterate(10)
+    assert done == 0
+    assert np.abs(c.get_p() - Oracle(p2).P0).max() < 1e-15
+
+
+def test_device_inputs_and_stream():
+    import torch
+    prob = I.diffusion3d_fv(12, 3)
+    dev = [torch.from_numpy(np.ascontiguousarray(a)).cuda() for a in prob.arrays()]
+    torch.cuda.synchronize()
+    s = torch.cuda.Stream()
+    with torch.cuda.stream(s):
+        from paper_2208_02995_gb300.emin import Context
+        c = Context(n=prob.n, nc=prob.nc, k=prob.k, arrays=dev)
+        c.iterate(8)
+        out = torch.empty(prob.nnz_p, dtype=torch.float64, device="cuda")
+        c.get_p(out)
+    s.synchronize()
+    ref = Oracle(prob).minimize(8)["P"]
+    assert relf(out.cpu().numpy(), ref) <= FP64_TOL
+
+
+def test_empty_problem():
+    z = np.zeros(1, dtype=np.int32)
+    p = I.Problem("empty", 0, 3, 1, z, np.zeros(0, np.int32), np.zeros(0), z,
+                  np.zeros(0, np.int32), np.zeros(0), np.zeros((0, 1)), np.ones((3, 1)))
+    c = ctx(p)
+    assert c.iterate(3) == (0, 0.0)
+    assert c.get_p().shape == (0,)
+    assert c.energy() == 0.0
+
+
+# ---------------------------------------------------------------------------
+# errors: every case returns a status; none faults the device
+# ---------------------------------------------------------------------------
+def _expect(status, prob, **kw):
+    from paper_2208_02995_gb300.emin import EminError
+    with pytest.raises(EminError) as e:
+        ctx(prob, **kw)
+    assert e.value.status == status
+
+
+def test_invalid_inputs_are_rejected():
+    from paper_2208_02995_gb300 import emin as E
+    base = I.random_problem(40, 12, 1, seed=4)
+
+    def mod(**kw):
+        d = dict(name="bad", n=base.n, nc=base.nc, k=base.k, A_rowptr=base.A_rowptr.copy(),
+                 A_col=base.A_col.copy(), A_val=base.A_val.copy(), P_rowptr=base.P_rowptr.copy(),
+                 P_col=base.P_col.copy(), P0_val=base.P0_val.copy(), B=base.B.copy(),
+                 Bc=base.Bc.copy())
+        d.update(kw)
+        return I.Problem(**d)
+
+    c = base.A_col.copy(); c[5] = base.n + 3
+    _expect(E.EMIN_ERR_PATTERN, mod(A_col=c))
+    c = base.P_col.copy(); c[7] = -1
+    _expect(E.EMIN_ERR_PATTERN, mod(P_col=c))
+    c = base.P_col.copy(); s0 = base.P_rowptr[2]; c[s0 + 1] = c[s0]
+    _expect(E.EMIN_ERR_PATTERN, mod(P_col=c))
+    rp = base.A_rowptr.copy(); rp[3] = rp[4] + 1
+    _expect(E.EMIN_ERR_PATTERN, mod(A_rowptr=rp))
+    v = base.A_val.copy()
+    rows = np.repeat(np.arange(base.n), np.diff(base.A_rowptr))
+    v[(rows == 6) & (base.A_col == 6)] = -1.0
+    _expect(E.EMIN_ERR_DIAG, mod(A_val=v))
+    v = base.A_val.copy(); v[3] = np.nan
+    _expect(E.EMIN_ERR_ARG, mod(A_val=v))
+
+
+def test_rank_policy():
+    from paper_2208_02995_gb300 import emin as E
+    prob = I.random_problem(20, 9, 3, p_per_row=4, seed=11)
+    Pp, Pj, P0 = prob.P_rowptr.copy(), prob.P_col.copy(), prob.P0_val.copy()
+    s0, s1 = Pp[5], Pp[6]
+    drop = np.arange(s0 + 2, s1)
+    Pj, P0 = np.delete(Pj, drop), np.delete(P0, drop)
+    Pp[6:] -= len(drop)
+    p2 = I.Problem("rankdef", prob.n, prob.nc, 3, prob.A_rowptr, prob.A_col, prob.A_val,
+                   Pp, Pj, P0, prob.B, prob.Bc)
+    _expect(E.EMIN_ERR_RANK, p2)
+    c = ctx(p2, rank_policy="pinv")
+    assert c.stats()["n_rank_deficient"] == 1
+    o = Oracle(p2, pinv=True)
+    assert np.abs(c.get_p() - o.P0).max() < 1e-12
+    ref = o.minimize(8)
+    c.iterate(8)
+    assert relf(c.get_p(), ref["P"]) <= FP64_TOL
+
+
+# ---------------------------------------------------------------------------
+# adjoint
+# ---------------------------------------------------------------------------
+@pytest.mark.parametrize("prob", [I.poisson2d(10, 2), I.elasticity3d(4, 0.3, 2),
+                                  I.random_problem(60, 20, 2, p_per_row=6, seed=7)],
+                         ids=lambda p: p.name)
+def test_outer_and_backward_match_oracle(prob):
+    o = Oracle(prob)
+    ref = o.minimize(400)
+    P = ref["P"]
+    c = ctx(prob)
+    c.iterate(400)
+    Pg = c.get_p()
+    rng = np.random.default_rng(3)
+    U, V = rng.standard_normal((2, prob.nnz_p))
+    assert np.abs(c.outer(U, V) - o.outer(U, V)).max() <= 1e-12 * np.abs(o.outer(U, V)).max()
+    dLdP = 2 * o.kprod(P) + 2 * P
+    dA_ref, dB_ref, _, _ = o.backward(P, dLdP, 400)
+    dA, dB, it = c.backward(dLdP, 400, 0.0)
+    assert relf(dA, dA_ref) <= 1e-8
+    assert relf(dB, dB_ref) <= 1e-8
+
+
+@pytest.mark.parametrize("precision", ["fp64", "mixed"])
+def test_workload2_full_size(precision):
+    """3D FV diffusion 128^3 (2.1M rows), 20 iterations, the launch
+    configuration the benchmark times: element-wise against the oracle."""
+    prob = I.config(2)
+    o = Oracle(prob)
+    ref = o.minimize(prob.iters, 0.0)
+    c = ctx(prob, precision)
+    done, _ = c.iterate(prob.iters, 0.0)
+    assert done == ref["applied"] == prob.iters
+    P = c.get_p()
+    if precision == "fp64":
+        assert relf(P, ref["P"]) <= FP64_TOL
+        assert np.allclose(c.stats()["dE"], ref["dE"], rtol=1e-9, atol=1e-13 * ref["dE"][0])
+    else:
+        Eref = o.energy(ref["P"])
+        assert abs(c.energy() - Eref) <= MIXED_E_TOL * abs(Eref)
+        assert relf(P, ref["P"]) <= 1e-4
+    assert o.constraint_error(P) <= CONSTRAINT_TOL
