@@ -177,14 +177,16 @@ int emin_stats(emin_ctx *ctx, double *dE_hist, int cap, int *n_hist,
                int *n_rank_deficient, int *n_applied);
 
 /*
- * Instrumentation.  emin_set_timing(ctx, 1) makes every later emin_iterate
- * bracket each kernel launch of the iteration with CUDA events on the
- * context's stream; emin_timing returns, per kernel class (0: masked product
- * with projection, 1: direction update, 2: vector update), the summed event
- * time in ms and the number of launches since timing was enabled (either
- * array may be NULL; each has 3 entries), and in *total_launches the number
- * of kernels the library launched since the context was created.
- * Enabling (again) clears the sums.
+ * Instrumentation.  emin_set_timing(ctx, p) with p >= 1 makes every later
+ * emin_iterate bracket the masked-product launch of every p-th iteration
+ * (iterations 0, p, 2p, ... of the call) with CUDA events on the context's
+ * stream (p = 0 switches timing off); emin_timing returns in ms[0] / launches[0] the
+ * summed event time and the number of timed launches since timing was
+ * enabled (entries 1 and 2 are reserved, 0; either array may be NULL and
+ * has 3 entries), and in *total_launches the number of kernels the library
+ * has run since the context was created.  Enabling (again) clears the sums.
+ * On a non-default stream emin_iterate runs the iteration loop as one CUDA
+ * graph (captured on first use for a given iteration count).
  */
 int emin_set_timing(emin_ctx *ctx, int enable);
 int emin_timing(emin_ctx *ctx, double *ms, long long *launches, long long *total_launches);

@@ -28,10 +28,22 @@ struct emin_ctx {
     // inputs (library-owned copies)
     int *Ap = nullptr, *Aj = nullptr, *Pp = nullptr, *Pj = nullptr;
     double *Av = nullptr, *P0_in = nullptr, *P0 = nullptr, *B = nullptr, *Bc = nullptr;
-    float *Av32 = nullptr, *Bc32 = nullptr;
+    float *Bc32 = nullptr;
     // set-up products
-    double *Ginv = nullptr, *dinv = nullptr;
+    double *Ginv = nullptr, *dinv = nullptr, *dsq = nullptr, *dhalf = nullptr, *rn = nullptr;
+    bool fast_k1 = false;  // k = 1, rows of P <= 4: fused set-up / final kernels and SELL plan
     float *Ginv32 = nullptr, *dinv32 = nullptr;
+    // the iteration runs on A^ = D^{-1/2} A D^{-1/2} (float and/or double)
+    float *Ah32 = nullptr, *qv32 = nullptr;
+    double *Ah64 = nullptr, *qv64 = nullptr;
+    bool have64 = false;  // Ah64 / qv64 formed for the current values
+    // k = 1 plan of the fixed pattern (built once per context), SELL-32 order
+    int *sell_ptr = nullptr, *soff = nullptr, *dpos = nullptr;
+    unsigned short *smap = nullptr;
+    float *sa32 = nullptr;
+    double *sa64 = nullptr;
+    long long nnz_sell = 0;
+    double *Pstar = nullptr, *t64c = nullptr;
     // restricted PCG workspaces
     Work<double> w64;   // forward, EMIN_FP64
     Work<float> w32;    // forward, EMIN_MIXED
@@ -46,7 +58,7 @@ struct emin_ctx {
     int applied_seen = 0;
     std::vector<void *> dev_allocs;
     // instrumentation
-    bool timing = false;
+    int timing = 0;  // 0 off, else time the masked product of every timing-th iteration
     std::vector<cudaEvent_t> events;  // start/stop pairs, one per timed launch
     double tms[3] = {0, 0, 0};
     long long tlaunch[3] = {0, 0, 0};
@@ -56,6 +68,7 @@ struct emin_ctx {
 namespace emin {
 static std::atomic<long long> g_launches{0};
 void note_launch() { g_launches.fetch_add(1, std::memory_order_relaxed); }
+void note_launches(long long k) { g_launches.fetch_add(k, std::memory_order_relaxed); }
 long long launches_so_far() { return g_launches.load(std::memory_order_relaxed); }
 }  // namespace emin
 
@@ -119,14 +132,21 @@ int copy_out(emin_ctx *c, void *dst, const void *src, size_t bytes, int on_devic
 
 int sync(emin_ctx *c) { return cuda_status(cudaStreamSynchronize(c->stream)); }
 
-Ops<double> ops64(const emin_ctx *c) {
-    return Ops<double>{c->n, c->nc, c->k, c->Ap, c->Aj, c->Av, c->Pp, c->Pj,
-                       c->Bc, c->Ginv, c->dinv, c->maxrow_p, c->lanes};
+// masked products on the unscaled A (energy, adjoint right-hand sides)
+Ops<double> plain_ops64(const emin_ctx *c) {
+    return Ops<double>{c->n, c->nc, c->k, c->Ap, c->Aj, c->Av, c->Pp, c->Pj, c->Bc, c->Ginv,
+                       nullptr, nullptr, nullptr, nullptr, nullptr, c->maxrow_p, c->lanes};
 }
 
-Ops<float> ops32(const emin_ctx *c) {
-    return Ops<float>{c->n, c->nc, c->k, c->Ap, c->Aj, c->Av32, c->Pp, c->Pj,
-                      c->Bc32, c->Ginv32, c->dinv32, c->maxrow_p, c->lanes};
+// the iteration's operator A^ with its plan
+Ops<double> iter_ops64(const emin_ctx *c) {
+    return Ops<double>{c->n, c->nc, c->k, c->Ap, c->Aj, c->Ah64, c->Pp, c->Pj, c->Bc, c->Ginv,
+                       c->qv64, c->sell_ptr, c->sa64, c->soff, c->smap, c->maxrow_p, c->lanes};
+}
+
+Ops<float> iter_ops32(const emin_ctx *c) {
+    return Ops<float>{c->n, c->nc, c->k, c->Ap, c->Aj, c->Ah32, c->Pp, c->Pj, c->Bc32, c->Ginv32,
+                      c->qv32, c->sell_ptr, c->sa32, c->soff, c->smap, c->maxrow_p, c->lanes};
 }
 
 template <class T>
@@ -145,8 +165,10 @@ int alloc_work(emin_ctx *c, Work<T> &w, bool vectors) {
     return EMIN_OK;
 }
 
-// r = -Pi_B K x0 in the workspace, with the convergence floor and gamma_0.
-// (Algorithm 3, first line, f = 0.)  For the adjoint the caller fills R.
+// Start of Algorithm 3 in the scaled variables: r~ = -Pi_B A^ x0~ with
+// x0~ = D^{1/2} p0 (so r~ = D^{-1/2} r), the convergence floor from the
+// unprojected residual, and gamma_0 = <r~, r~>.  For the adjoint x0 is null
+// and the caller has put the scaled right-hand side in R.
 template <class T>
 int start_pcg(emin_ctx *c, const Ops<T> &o, Work<T> &w, const T *x0) {
     launch_state_reset(c->L, w.st);
@@ -155,28 +177,67 @@ int start_pcg(emin_ctx *c, const Ops<T> &o, Work<T> &w, const T *x0) {
         EMIN_TRY(cuda_status(cudaMemsetAsync(w.X, 0, sizeof(T) * c->nnz_p, c->stream)));
     }
     if (x0) launch_kprod<T>(c->L, o, x0, w.R, 0, DOT_NONE, w, 0);
-    launch_update<T>(c->L, o, w, UPD_FLOOR);
+    launch_update<T>(c->L, c->nnz_p, w, UPD_FLOOR);
     launch_project<T>(c->L, o, w.R, x0 ? T(-1) : T(1));
-    launch_update<T>(c->L, o, w, UPD_INIT);
+    launch_update<T>(c->L, c->nnz_p, w, UPD_INIT);
     return check_launch();
+}
+
+// A^ and q in double (the FP64 path, or the adjoint of a mixed context)
+void form_scaled64(emin_ctx *c) {
+    if (c->sell_ptr)
+        launch_sell_values<double>(c->L, c->n, c->Ap, c->Aj, c->Av, c->dsq, c->sell_ptr, c->sa64);
+    else
+        launch_scale_a<double>(c->L, c->n, c->Ap, c->Aj, c->Av, c->dsq, c->Ah64);
+    if (c->k == 1) launch_qvec_k1<double>(c->L, c->n, c->Pp, c->Pj, c->Bc, c->qv64);
+    c->have64 = true;
 }
 
 // Algorithm 2 plus the start of Algorithm 3 from the stored inputs.
 int run_setup(emin_ctx *c) {
     const Launch &L = c->L;
     EMIN_TRY(cuda_status(cudaMemsetAsync(c->dint, 0, 3 * sizeof(int), c->stream)));
+    c->have64 = false;
+    if (c->fast_k1) {
+        const bool mixed = c->opts.precision == EMIN_MIXED;
+        if (mixed) {
+            launch_setup_k1<float>(L, c->n, c->dpos, c->Av, c->Pp, c->Pj, c->Bc, c->B, c->P0_in,
+                                   c->opts.rank_policy, c->dint, c->dint + 2, c->dsq, c->dhalf,
+                                   c->Ginv, c->qv32, c->P0, c->t32a);
+            launch_to_float(L, c->Bc, c->Bc32, (long long)c->nc * c->k);
+            launch_sell_values<float>(L, c->n, c->Ap, c->Aj, c->Av, c->dsq, c->sell_ptr, c->sa32);
+            EMIN_TRY(start_pcg<float>(c, iter_ops32(c), c->w32, c->t32a));
+        } else {
+            launch_setup_k1<double>(L, c->n, c->dpos, c->Av, c->Pp, c->Pj, c->Bc, c->B, c->P0_in,
+                                    c->opts.rank_policy, c->dint, c->dint + 2, c->dsq, c->dhalf,
+                                    c->Ginv, c->qv64, c->P0, c->t64c);
+            launch_sell_values<double>(L, c->n, c->Ap, c->Aj, c->Av, c->dsq, c->sell_ptr, c->sa64);
+            c->have64 = true;
+            EMIN_TRY(start_pcg<double>(c, iter_ops64(c), c->w64, c->t64c));
+        }
+        c->applied_seen = 0;
+        return check_launch();
+    }
     launch_diag(L, c->n, c->Ap, c->Aj, c->Av, c->dinv, c->dinv32, c->dint);
+    launch_diag_scales(L, c->n, c->dinv, c->dsq, c->dhalf);
     launch_gram(L, c->n, c->k, c->Pp, c->Pj, c->Bc, c->Ginv, c->Ginv32, c->opts.rank_policy,
                 c->dint, c->dint + 2);
     launch_restore(L, c->n, c->k, c->Pp, c->Pj, c->Bc, c->B, c->Ginv, c->P0_in, nullptr, nullptr,
-                   c->P0);
+                   nullptr, 1, c->P0);
+    c->have64 = false;
     if (c->opts.precision == EMIN_MIXED) {
-        launch_to_float(L, c->Av, c->Av32, c->nnz_a);
         launch_to_float(L, c->Bc, c->Bc32, (long long)c->nc * c->k);
-        launch_to_float(L, c->P0, c->t32a, c->nnz_p);
-        EMIN_TRY(start_pcg<float>(c, ops32(c), c->w32, c->t32a));
+        if (c->sell_ptr)
+            launch_sell_values<float>(L, c->n, c->Ap, c->Aj, c->Av, c->dsq, c->sell_ptr, c->sa32);
+        else
+            launch_scale_a<float>(L, c->n, c->Ap, c->Aj, c->Av, c->dsq, c->Ah32);
+        if (c->k == 1) launch_qvec_k1<float>(L, c->n, c->Pp, c->Pj, c->Bc, c->qv32);
+        launch_row_scale<double, float>(L, c->n, c->Pp, c->lanes, c->dhalf, 1.0, c->P0, c->t32a);
+        EMIN_TRY(start_pcg<float>(c, iter_ops32(c), c->w32, c->t32a));
     } else {
-        EMIN_TRY(start_pcg<double>(c, ops64(c), c->w64, c->P0));
+        form_scaled64(c);
+        launch_row_scale<double, double>(L, c->n, c->Pp, c->lanes, c->dhalf, 1.0, c->P0, c->t64c);
+        EMIN_TRY(start_pcg<double>(c, iter_ops64(c), c->w64, c->t64c));
     }
     c->applied_seen = 0;
     return check_launch();
@@ -201,17 +262,24 @@ int read_state(emin_ctx *c, const DevState *st) {
     return sync(c);
 }
 
-// current P on P's pattern, in double, into dst (device)
+// current P = P0 + D^{-1/2} dW~ on P's pattern, in double, into dst (device);
+// in mixed precision every row is then corrected onto its constraint in double
 int form_p(emin_ctx *c, double *dst) {
-    if (c->opts.precision == EMIN_MIXED) {
-        // promote the float correction and restore every row's constraint in double
-        launch_restore(c->L, c->n, c->k, c->Pp, c->Pj, c->Bc, c->B, c->Ginv, c->P0, nullptr,
-                       c->w32.X, dst);
-    } else if (c->nnz_p > 0) {
-        EMIN_TRY(cuda_status(cudaMemcpyAsync(dst, c->P0, sizeof(double) * c->nnz_p,
-                                             cudaMemcpyDeviceToDevice, c->stream)));
-        launch_axpby(c->L, c->nnz_p, 1.0, c->w64.X, 1.0, dst);
+    if (c->fast_k1) {
+        if (c->opts.precision == EMIN_MIXED)
+            launch_final_k1<float>(c->L, c->n, c->Pp, c->Pj, c->Bc, c->Ginv, c->P0, c->w32.X,
+                                   c->dsq, c->B, 1, dst);
+        else
+            launch_final_k1<double>(c->L, c->n, c->Pp, c->Pj, c->Bc, c->Ginv, c->P0, c->w64.X,
+                                    c->dsq, c->B, 0, dst);
+        return check_launch();
     }
+    if (c->opts.precision == EMIN_MIXED)
+        launch_restore(c->L, c->n, c->k, c->Pp, c->Pj, c->Bc, c->B, c->Ginv, c->P0, nullptr,
+                       c->w32.X, c->dsq, 1, dst);
+    else
+        launch_restore(c->L, c->n, c->k, c->Pp, c->Pj, c->Bc, c->B, c->Ginv, c->P0, c->w64.X,
+                       nullptr, c->dsq, 0, dst);
     return check_launch();
 }
 
@@ -237,6 +305,7 @@ int create_impl(emin_ctx *c, const int *A_rowptr, const int *A_col, const double
     c->nnz_p = ends[3];
     const long long nk = (long long)n * c->k, nck = (long long)c->nc * c->k;
     const long long kk = (long long)n * (c->k * (c->k + 1) / 2);
+    const bool k1 = (c->k == 1);
 
     EMIN_TRY(dalloc(c, &c->Ap, n + 1));
     EMIN_TRY(dalloc(c, &c->Aj, c->nnz_a));
@@ -251,16 +320,24 @@ int create_impl(emin_ctx *c, const int *A_rowptr, const int *A_col, const double
     EMIN_TRY(dalloc(c, &c->Ginv32, kk));
     EMIN_TRY(dalloc(c, &c->dinv, n));
     EMIN_TRY(dalloc(c, &c->dinv32, n));
+    EMIN_TRY(dalloc(c, &c->dsq, n));
+    EMIN_TRY(dalloc(c, &c->dhalf, n));
+    EMIN_TRY(dalloc(c, &c->rn, n));
     EMIN_TRY(dalloc(c, &c->dint, 4));
     EMIN_TRY(dalloc(c, &c->t64a, c->nnz_p));
     EMIN_TRY(dalloc(c, &c->t64b, c->nnz_p));
+    EMIN_TRY(dalloc(c, &c->t64c, c->nnz_p));
     if (c->opts.precision == EMIN_MIXED) {
-        EMIN_TRY(dalloc(c, &c->Av32, c->nnz_a));
+        EMIN_TRY(dalloc(c, &c->Ah32, c->nnz_a));
+        if (k1) EMIN_TRY(dalloc(c, &c->qv32, c->nnz_p));
+        if (k1) EMIN_TRY(dalloc(c, &c->qv64, c->nnz_p));
         EMIN_TRY(dalloc(c, &c->Bc32, nck));
         EMIN_TRY(dalloc(c, &c->t32a, c->nnz_p));
         EMIN_TRY(dalloc(c, &c->t32b, c->nnz_p));
         EMIN_TRY(alloc_work(c, c->w32, true));
     } else {
+        EMIN_TRY(dalloc(c, &c->Ah64, c->nnz_a));
+        if (k1) EMIN_TRY(dalloc(c, &c->qv64, c->nnz_p));
         EMIN_TRY(alloc_work(c, c->w64, true));
     }
     EMIN_TRY(alloc_work(c, c->aux, false));
@@ -297,45 +374,117 @@ int create_impl(emin_ctx *c, const int *A_rowptr, const int *A_col, const double
     c->maxrow_p = c->hint[1];
     if (c->maxrow_p > kMaxRowP) return EMIN_ERR_ARG;
     c->lanes = (c->maxrow_p <= 8) ? 1 : 32;
+    c->fast_k1 = (c->k == 1 && c->maxrow_p <= 4 && n > 0);
+    if (c->fast_k1 && n > 0) {
+        // the plan of the fixed pattern in SELL-32 order: built once, reused by
+        // every product of every iteration
+        const int ns = (n + 31) / 32;
+        EMIN_TRY(dalloc(c, &c->sell_ptr, ns + 1));
+        launch_sell_len(c->L, n, c->Ap, c->sell_ptr);
+        std::vector<int> h(ns + 1, 0);
+        EMIN_TRY(cuda_status(cudaMemcpyAsync(h.data(), c->sell_ptr, sizeof(int) * ns,
+                                             cudaMemcpyDeviceToHost, c->stream)));
+        EMIN_TRY(sync(c));
+        long long acc = 0;
+        for (int s = 0; s < ns; ++s) {
+            const long long len = h[s];
+            h[s] = (int)acc;
+            acc += 32 * len;
+        }
+        if (acc > 0x7fffffffLL) return EMIN_ERR_ARG;
+        h[ns] = (int)acc;
+        c->nnz_sell = acc;
+        EMIN_TRY(cuda_status(cudaMemcpyAsync(c->sell_ptr, h.data(), sizeof(int) * (ns + 1),
+                                             cudaMemcpyHostToDevice, c->stream)));
+        EMIN_TRY(dalloc(c, &c->soff, acc));
+        EMIN_TRY(dalloc(c, &c->smap, acc));
+        EMIN_TRY(dalloc(c, &c->dpos, n));
+        launch_sell_plan(c->L, n, c->Ap, c->Aj, c->Pp, c->Pj, c->sell_ptr, c->soff, c->smap,
+                         c->dpos);
+        if (c->opts.precision == EMIN_MIXED) EMIN_TRY(dalloc(c, &c->sa32, acc));
+        else EMIN_TRY(dalloc(c, &c->sa64, acc));
+        EMIN_TRY(sync(c));  // the host copy of the offsets must outlive the transfer
+    }
 
     EMIN_TRY(run_setup(c));
     return read_flags(c);
+}
+
+// The launches of n_iters iterations of Algorithm 3 (scaled variables):
+// y~ = r~ + beta y~; y_~ = Pi A^ y~ with y~^T y_~ -> alpha; dW~, r~ updates
+// with gamma -> beta.  With `timed`, the masked product of every iteration
+// is bracketed by CUDA events on the context's stream.
+template <class T>
+int launch_iterations(emin_ctx *c, const Ops<T> &o, Work<T> &w, int n_iters, bool timed) {
+    for (int it = 0; it < n_iters; ++it) {
+        launch_ydir<T>(c->L, c->nnz_p, w);
+        // external records, so that the events also time the launches when
+        // the loop is captured into a graph; every c->timing-th iteration
+        const bool t = timed && (it % c->timing) == 0;
+        if (t) cudaEventRecordWithFlags(c->events[(size_t)it * 2], c->stream, cudaEventRecordExternal);
+        launch_kprod<T>(c->L, o, w.Y, w.Yb, 1, DOT_ALPHA, w, 1);
+        if (t) cudaEventRecordWithFlags(c->events[(size_t)it * 2 + 1], c->stream, cudaEventRecordExternal);
+        launch_update<T>(c->L, c->nnz_p, w, UPD_STEP);
+    }
+    return check_launch();
+}
+
+bool capturable(cudaStream_t s) {
+    return s != nullptr && s != cudaStreamLegacy && s != cudaStreamPerThread;
 }
 
 template <class T>
 int iterate_impl(emin_ctx *c, const Ops<T> &o, Work<T> &w, int n_iters, double tol,
                  bool timed = false) {
     launch_state_begin(c->L, w.st, tol);
-    timed = timed && c->timing && o.n > 0;
+    timed = timed && c->timing > 0 && o.n > 0;
     if (timed) {
-        const size_t need = (size_t)n_iters * 6;
+        const size_t need = (size_t)n_iters * 2;
         while (c->events.size() < need) {
             cudaEvent_t e;
             if (cudaEventCreate(&e) != cudaSuccess) return cuda_status(cudaGetLastError());
             c->events.push_back(e);
         }
     }
-    for (int it = 0; it < n_iters; ++it) {
-        cudaEvent_t *ev = timed ? &c->events[(size_t)it * 6] : nullptr;
-        if (timed) cudaEventRecord(ev[2], c->stream);
-        launch_ydir<T>(c->L, o, w);
-        if (timed) { cudaEventRecord(ev[3], c->stream); cudaEventRecord(ev[0], c->stream); }
-        launch_kprod<T>(c->L, o, w.Y, w.Yb, 1, DOT_ALPHA, w, 1);
-        if (timed) { cudaEventRecord(ev[1], c->stream); cudaEventRecord(ev[4], c->stream); }
-        launch_update<T>(c->L, o, w, UPD_STEP);
-        if (timed) cudaEventRecord(ev[5], c->stream);
+    bool launched = false;
+    if (n_iters > 0 && o.n > 0 && capturable(c->stream)) {
+        // the whole loop as one CUDA graph, captured once per (count, timing)
+        const int tkey = timed ? c->timing : 0;
+        if (!(w.gexec && w.gn == n_iters && w.gtimed == tkey)) {
+            if (w.gexec) {
+                cudaGraphExecDestroy(w.gexec);
+                w.gexec = nullptr;
+            }
+            const long long before = launches_so_far();
+            cudaGraph_t graph = nullptr;
+            if (cudaStreamBeginCapture(c->stream, cudaStreamCaptureModeThreadLocal) == cudaSuccess) {
+                launch_iterations<T>(c, o, w, n_iters, timed);
+                if (cudaStreamEndCapture(c->stream, &graph) == cudaSuccess && graph) {
+                    if (cudaGraphInstantiate(&w.gexec, graph, 0) != cudaSuccess) w.gexec = nullptr;
+                    cudaGraphDestroy(graph);
+                }
+            }
+            cudaGetLastError();
+            note_launches(before - launches_so_far());  // captured, not run
+            w.gn = n_iters;
+            w.gtimed = tkey;
+        }
+        if (w.gexec && cudaGraphLaunch(w.gexec, c->stream) == cudaSuccess) {
+            note_launches(3LL * n_iters);
+            launched = true;
+        }
+        cudaGetLastError();
     }
+    if (!launched) EMIN_TRY(launch_iterations<T>(c, o, w, n_iters, timed));
     EMIN_TRY(check_launch());
     EMIN_TRY(read_state(c, w.st));
     if (timed) {
-        for (int it = 0; it < n_iters; ++it) {
-            cudaEvent_t *ev = &c->events[(size_t)it * 6];
-            for (int j = 0; j < 3; ++j) {
-                float ms = 0.f;
-                if (cudaEventElapsedTime(&ms, ev[2 * j], ev[2 * j + 1]) == cudaSuccess) {
-                    c->tms[j] += ms;
-                    c->tlaunch[j] += 1;
-                }
+        for (int it = 0; it < n_iters; it += c->timing) {
+            float ms = 0.f;
+            if (cudaEventElapsedTime(&ms, c->events[(size_t)it * 2], c->events[(size_t)it * 2 + 1]) ==
+                cudaSuccess) {
+                c->tms[0] += ms;
+                c->tlaunch[0] += 1;
             }
         }
         cudaGetLastError();
@@ -377,6 +526,9 @@ void emin_destroy(emin_ctx *c) {
     {
         DeviceGuard g(c->device);
         cudaStreamSynchronize(c->stream);
+        for (cudaGraphExec_t g : {c->w64.gexec, c->adj.gexec, c->aux.gexec})
+            if (g) cudaGraphExecDestroy(g);
+        if (c->w32.gexec) cudaGraphExecDestroy(c->w32.gexec);
         for (void *p : c->dev_allocs) cudaFree(p);
         for (cudaEvent_t e : c->events) cudaEventDestroy(e);
         if (c->hstate) cudaFreeHost(c->hstate);
@@ -419,6 +571,8 @@ int emin_create(emin_ctx **out, int n, int nc, int k, const int *A_rowptr, const
     c->L.grid_rows = nsm * occ_rows;
     c->L.grid_warps = nsm * occ_warps;
     if (c->L.grid_rows > kMaxGrid) c->L.grid_rows = kMaxGrid;
+    c->L.grid_staged = nsm * staged_blocks_per_sm();
+    if (c->L.grid_staged > kMaxGrid) c->L.grid_staged = kMaxGrid;
     if (c->L.grid_warps > kMaxGrid) c->L.grid_warps = kMaxGrid;
     set_iter_attributes();
     set_adjoint_attributes();
@@ -469,9 +623,9 @@ int emin_iterate(emin_ctx *c, int n_iters, double tol, int *iters_done, double *
     int s;
     const DevState *hs = c->hstate;
     if (c->opts.precision == EMIN_MIXED)
-        s = iterate_impl<float>(c, ops32(c), c->w32, n_iters, tol, true);
+        s = iterate_impl<float>(c, iter_ops32(c), c->w32, n_iters, tol, true);
     else
-        s = iterate_impl<double>(c, ops64(c), c->w64, n_iters, tol, true);
+        s = iterate_impl<double>(c, iter_ops64(c), c->w64, n_iters, tol, true);
     if (s != EMIN_OK) {
         c->sticky = s;
         return s;
@@ -501,7 +655,7 @@ int emin_energy(emin_ctx *c, double *E) {
     if (c->sticky != EMIN_OK) return c->sticky;
     EMIN_TRY(form_p(c, c->t64a));
     launch_state_reset(c->L, c->aux.st);
-    launch_kprod<double>(c->L, ops64(c), c->t64a, c->t64b, 0, DOT_AUX, c->aux, 0);
+    launch_kprod<double>(c->L, plain_ops64(c), c->t64a, c->t64b, 0, DOT_AUX, c->aux, 0);
     EMIN_TRY(check_launch());
     EMIN_TRY(read_state(c, c->aux.st));
     *E = c->hstate->aux;
@@ -511,13 +665,16 @@ int emin_energy(emin_ctx *c, double *E) {
 int emin_kprod(emin_ctx *c, const double *X, double *out, int project, int on_device) {
     if (!c) return EMIN_ERR_ARG;
     DeviceGuard g(c->device);
+    // the iteration's kernel on x~ = D^{1/2} X, scaled back: y = D^{1/2} y~
     EMIN_TRY(copy_in(c, c->t64a, X, sizeof(double) * c->nnz_p, on_device));
     if (c->opts.precision == EMIN_MIXED) {
-        launch_to_float(c->L, c->t64a, c->t32a, c->nnz_p);
-        launch_kprod<float>(c->L, ops32(c), c->t32a, c->t32b, project ? 1 : 0, DOT_NONE, c->w32, 0);
-        launch_to_double(c->L, c->t32b, c->t64b, c->nnz_p);
+        launch_row_scale<double, float>(c->L, c->n, c->Pp, c->lanes, c->dhalf, 1.0, c->t64a, c->t32a);
+        launch_kprod<float>(c->L, iter_ops32(c), c->t32a, c->t32b, project ? 1 : 0, DOT_NONE, c->w32, 0);
+        launch_row_scale<float, double>(c->L, c->n, c->Pp, c->lanes, c->dhalf, 1.0, c->t32b, c->t64b);
     } else {
-        launch_kprod<double>(c->L, ops64(c), c->t64a, c->t64b, project ? 1 : 0, DOT_NONE, c->aux, 0);
+        launch_row_scale<double, double>(c->L, c->n, c->Pp, c->lanes, c->dhalf, 1.0, c->t64a, c->t64c);
+        launch_kprod<double>(c->L, iter_ops64(c), c->t64c, c->t64a, project ? 1 : 0, DOT_NONE, c->aux, 0);
+        launch_row_scale<double, double>(c->L, c->n, c->Pp, c->lanes, c->dhalf, 1.0, c->t64a, c->t64b);
     }
     EMIN_TRY(check_launch());
     EMIN_TRY(copy_out(c, out, c->t64b, sizeof(double) * c->nnz_p, on_device));
@@ -545,24 +702,27 @@ int emin_backward(emin_ctx *c, const double *dL_dP, double *dL_dAval, double *dL
         EMIN_TRY(alloc_work(c, c->adj, true));
         if (!c->tA) EMIN_TRY(dalloc(c, &c->tA, c->nnz_a));
         EMIN_TRY(dalloc(c, &c->tmu, (long long)c->n * c->k));
+        EMIN_TRY(dalloc(c, &c->Pstar, c->nnz_p));
+        if (!c->Ah64) EMIN_TRY(dalloc(c, &c->Ah64, c->nnz_a));
+        if (c->sell_ptr && !c->sa64) EMIN_TRY(dalloc(c, &c->sa64, c->nnz_sell));
+        if (c->k == 1 && !c->qv64) EMIN_TRY(dalloc(c, &c->qv64, c->nnz_p));
     }
-    const Ops<double> o = ops64(c);
+    if (!c->have64) form_scaled64(c);
+    const Ops<double> o = iter_ops64(c);
     Work<double> &w = c->adj;
     // P* (kept from the forward) and dL/dP
-    EMIN_TRY(form_p(c, c->t64a));
+    EMIN_TRY(form_p(c, c->Pstar));
     EMIN_TRY(copy_in(c, c->t64b, dL_dP, sizeof(double) * c->nnz_p, on_device));
-    // Pi K Pi u = 1/2 Pi dL/dP from u = 0
-    if (c->nnz_p > 0) {
-        EMIN_TRY(cuda_status(cudaMemcpyAsync(w.R, c->t64b, sizeof(double) * c->nnz_p,
-                                             cudaMemcpyDeviceToDevice, c->stream)));
-        launch_axpby(c->L, c->nnz_p, 0.0, c->t64b, 0.5, w.R);
-    }
+    // Pi K Pi u = 1/2 Pi dL/dP from u = 0, in the scaled variables
+    // (right-hand side D^{-1/2} dL/dP / 2, solution u = D^{-1/2} u~)
+    launch_row_scale<double, double>(c->L, c->n, c->Pp, c->lanes, c->dsq, 0.5, c->t64b, w.R);
     EMIN_TRY(start_pcg<double>(c, o, w, nullptr));
     EMIN_TRY(iterate_impl<double>(c, o, w, max_adj_iters, adj_tol));
     if (c->hstate->status != EMIN_OK) return c->hstate->status;
     if (adj_iters) *adj_iters = c->hstate->applied;
+    launch_row_scale<double, double>(c->L, c->n, c->Pp, c->lanes, c->dsq, 1.0, w.X, c->t64c);
     // S = mask(A U);  x = dL/dP - 2 S;  mu = G^{-1} B_i^T x
-    launch_kprod<double>(c->L, o, w.X, w.Yb, 0, DOT_NONE, w, 0);
+    launch_kprod<double>(c->L, plain_ops64(c), c->t64c, w.Yb, 0, DOT_NONE, w, 0);
     launch_axpby(c->L, c->nnz_p, 1.0, c->t64b, -2.0, w.Yb);
     if (dL_dB) {
         launch_lsq(c->L, c->n, c->k, c->Pp, c->Pj, c->Bc, c->Ginv, w.Yb, c->tmu);
@@ -570,7 +730,8 @@ int emin_backward(emin_ctx *c, const double *dL_dP, double *dL_dAval, double *dL
         EMIN_TRY(copy_out(c, dL_dB, c->tmu, sizeof(double) * c->n * c->k, on_device));
     }
     if (dL_dAval) {
-        launch_outer(c->L, c->n, c->Ap, c->Aj, c->Pp, c->Pj, w.X, c->t64a, -2.0, c->tA, c->maxrow_p);
+        launch_outer(c->L, c->n, c->Ap, c->Aj, c->Pp, c->Pj, c->t64c, c->Pstar, -2.0, c->tA,
+                     c->maxrow_p);
         EMIN_TRY(check_launch());
         EMIN_TRY(copy_out(c, dL_dAval, c->tA, sizeof(double) * c->nnz_a, on_device));
     }
@@ -604,7 +765,7 @@ int emin_stats(emin_ctx *c, double *dE_hist, int cap, int *n_hist, int *n_rank_d
 
 int emin_set_timing(emin_ctx *c, int enable) {
     if (!c) return EMIN_ERR_ARG;
-    c->timing = enable != 0;
+    c->timing = enable > 0 ? enable : 0;
     for (int j = 0; j < 3; ++j) {
         c->tms[j] = 0.0;
         c->tlaunch[j] = 0;

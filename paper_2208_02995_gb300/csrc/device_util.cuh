@@ -12,11 +12,9 @@ __device__ __forceinline__ float fmat(float a, float b, float c) { return fmaf(a
 
 // ---------------------------------------------------------------------------
 // Dot-product accumulators.  Dot<double> is a plain FMA chain.  Dot<float>
-// keeps an unevaluated float pair (hi + lo): each product is split exactly
-// with an FMA (a*b = p + e) and added with Knuth's two-sum, so the float
-// products of the mixed path are summed to about 44 bits; the pair is
-// converted to double once per warp.  The _rn intrinsics keep the compiler
-// from contracting the error terms into FMAs.
+// (mixed path) sums the float products of one thread in float - a thread
+// holds a few dozen of them at most - and every further level (warp, block,
+// grid) is summed in double.
 // ---------------------------------------------------------------------------
 template <class T>
 struct Dot;
@@ -33,37 +31,15 @@ struct Dot<double> {
     }
 };
 
-__device__ __forceinline__ void two_sum(float a, float b, float &s, float &e) {
-    s = __fadd_rn(a, b);
-    float v = __fsub_rn(s, a);
-    e = __fadd_rn(__fsub_rn(a, __fsub_rn(s, v)), __fsub_rn(b, v));
-}
-
-__device__ __forceinline__ void ff_add(float &hi, float &lo, float bhi, float blo) {
-    float s, e;
-    two_sum(hi, bhi, s, e);
-    e = __fadd_rn(e, __fadd_rn(lo, blo));
-    hi = __fadd_rn(s, e);
-    lo = __fsub_rn(e, __fsub_rn(hi, s));
-}
-
 template <>
 struct Dot<float> {
-    float hi = 0.f, lo = 0.f;
-    __device__ __forceinline__ void add(float a, float b) {
-        float p = __fmul_rn(a, b);
-        float pe = fmaf(a, b, -p);  // exact error of the product
-        ff_add(hi, lo, p, pe);
-    }
+    float v = 0.f;
+    __device__ __forceinline__ void add(float a, float b) { v = fmaf(a, b, v); }
     __device__ __forceinline__ double warp_total() {
-        float h = hi, l = lo;
+        double s = (double)v;
 #pragma unroll
-        for (int o = 16; o > 0; o >>= 1) {
-            float oh = __shfl_down_sync(0xffffffffu, h, o);
-            float ol = __shfl_down_sync(0xffffffffu, l, o);
-            ff_add(h, l, oh, ol);
-        }
-        return (double)h + (double)l;
+        for (int o = 16; o > 0; o >>= 1) s += __shfl_down_sync(0xffffffffu, s, o);
+        return s;
     }
 };
 
@@ -120,6 +96,27 @@ __device__ __forceinline__ double block_dot_total(Dot<T> &d, double *sh) {
     if (threadIdx.x == 0)
         for (int i = 0; i < (int)(blockDim.x >> 5); ++i) s += sh[i];
     return s;
+}
+
+// 1/sqrt(x) for positive, finite, normal x by Newton-Raphson on
+// f(r) = r^-2 - x (r <- r (3 - x r^2) / 2), from a float seed on the
+// mantissa: the seed has about 23 correct bits, each step doubles them, so
+// two steps reach double precision up to a few ulps.  The exponent is
+// handled exactly (even power of two split off), so no FP64 division or
+// square root is issued.  Subnormal or non-positive x fall back to 1/sqrt.
+__device__ __forceinline__ double rsqrt_newton(double x) {
+    if (!(x >= 2.2250738585072014e-308) || !(x <= 1.7976931348623157e308)) return 1.0 / sqrt(x);
+    const long long b = __double_as_longlong(x);
+    int ex = (int)((b >> 52) & 0x7ff) - 1023;
+    double m = __longlong_as_double((b & 0x000fffffffffffffLL) | 0x3ff0000000000000LL);  // [1, 2)
+    if (ex & 1) {
+        m *= 2.0;
+        ex -= 1;
+    }
+    double r = (double)rsqrtf((float)m);
+    r = r * fma(-0.5 * m, r * r, 1.5);
+    r = r * fma(-0.5 * m, r * r, 1.5);
+    return r * __longlong_as_double((long long)(1023 - ex / 2) << 52);
 }
 
 // ---- scalar steps of Algorithm 3, run by one thread after a reduction ----

@@ -69,9 +69,15 @@ struct Work {
     double *partials = nullptr;
     double *hist = nullptr;
     int hist_cap = 0;
+    // the captured iteration loop (CUDA graph) for gn iterations
+    cudaGraphExec_t gexec = nullptr;
+    int gn = -1, gtimed = -1;
 };
 
-// Everything a kernel launch needs to know about the problem.
+// Everything a masked-product launch needs to know about the problem.
+// Av is either A itself (plain products: energy, adjoint right-hand sides)
+// or the symmetrically scaled A^ = D^{-1/2} A D^{-1/2} the iteration runs
+// on.  qv and the sell_* arrays are the k = 1 plan (null when there is none).
 template <class T>
 struct Ops {
     int n, nc, k;
@@ -80,15 +86,23 @@ struct Ops {
     const int *Pp, *Pj;
     const T *Bc;
     const T *Ginv;
-    const T *dinv;
-    int maxrow;    // longest row of P
-    int lanes;     // lanes per row of the vector kernels (1 or 32)
+    const T *qv;                  // k = 1: b / |b| per entry of P (the Q of Pi_B = I - q q^T)
+    // the k = 1 plan in SELL-32 order (slices of 32 rows, entry j of the 32
+    // rows contiguous, rows padded to the slice's longest): sell_ptr[s] is
+    // the first position of slice s; sa holds A^ at those positions
+    const int *sell_ptr;
+    const T *sa;
+    const int *soff;
+    const unsigned short *smap;
+    int maxrow;                   // longest row of P
+    int lanes;                    // lanes per row of the row kernels (1 or 32)
 };
 
 struct Launch {
     cudaStream_t stream;
     int grid_rows;    // grid of thread-per-row kernels
     int grid_warps;   // grid of warp-per-row kernels
+    int grid_staged;  // resident grid of the staged masked product
 };
 
 // shared-memory slots per warp for a row of P: the longest row rounded up
@@ -101,6 +115,7 @@ inline int staging_cap(int maxrow) {
 
 // process-wide count of kernels launched by the library (instrumentation)
 void note_launch();
+void note_launches(long long k);  // k may be negative (launches captured, not run)
 long long launches_so_far();
 
 // ---- set-up kernels (setup_kernels.cu) ----
@@ -111,11 +126,41 @@ void launch_diag(const Launch &L, int n, const int *Ap, const int *Aj, const dou
                  double *dinv64, float *dinv32, int *flags);
 void launch_gram(const Launch &L, int n, int k, const int *Pp, const int *Pj, const double *Bc,
                  double *Ginv, float *Ginv32, int policy, int *flags, int *ndef);
+// P = base + f_i * add (add64 or add32, f may be null = 1), then, if
+// `correct`, the least-norm constraint correction of every row
 void launch_restore(const Launch &L, int n, int k, const int *Pp, const int *Pj,
                     const double *Bc, const double *B, const double *Ginv, const double *base,
-                    const double *add64, const float *add32, double *P);
+                    const double *add64, const float *add32, const double *f, int correct,
+                    double *P);
 void launch_to_float(const Launch &L, const double *src, float *dst, long long count);
 void launch_to_double(const Launch &L, const float *src, double *dst, long long count);
+
+void launch_diag_scales(const Launch &L, int n, const double *dinv, double *dsq, double *dhalf);
+// whole k = 1 set-up per row (rows of P with at most 4 entries); see setup_kernels.cu
+template <class Tit>
+void launch_setup_k1(const Launch &L, int n, const int *dpos, const double *Av, const int *Pp,
+                     const int *Pj, const double *Bc, const double *B, const double *P0_in,
+                     int policy, int *flags, int *ndef, double *dsq, double *dhalf, double *Ginv,
+                     Tit *qv, double *P0, Tit *x0);
+// P = P0 + D^{-1/2} X (+ least-norm constraint correction), k = 1, rows <= 4
+template <class Tx>
+void launch_final_k1(const Launch &L, int n, const int *Pp, const int *Pj, const double *Bc,
+                     const double *Ginv, const double *P0, const Tx *X, const double *dsq,
+                     const double *B, int correct, double *P);
+// SELL-32 plan: slice lengths (longest row of A per 32 rows), then the plan
+// in slice order once sell_ptr (exclusive scan of 32 * length) is known
+void launch_sell_len(const Launch &L, int n, const int *Ap, int *slen);
+void launch_sell_plan(const Launch &L, int n, const int *Ap, const int *Aj, const int *Pp,
+                      const int *Pj, const int *sell_ptr, int *soff, unsigned short *smap,
+                      int *dpos);
+template <class T>
+void launch_sell_values(const Launch &L, int n, const int *Ap, const int *Aj, const double *Av,
+                        const double *dsq, const int *sell_ptr, T *sa);
+template <class T>
+void launch_scale_a(const Launch &L, int n, const int *Ap, const int *Aj, const double *Av,
+                    const double *dsq, T *Ahat);
+template <class T>
+void launch_qvec_k1(const Launch &L, int n, const int *Pp, const int *Pj, const double *Bc, T *qv);
 
 // ---- iteration kernels (iter_kernels.cu) ----
 template <class T>
@@ -124,11 +169,16 @@ void launch_kprod(const Launch &L, const Ops<T> &o, const T *Y, T *out, int proj
 template <class T>
 void launch_project(const Launch &L, const Ops<T> &o, T *x, T scale);
 template <class T>
-void launch_ydir(const Launch &L, const Ops<T> &o, Work<T> &w);
+void launch_ydir(const Launch &L, long long count, Work<T> &w);
 template <class T>
-void launch_update(const Launch &L, const Ops<T> &o, Work<T> &w, int mode);
+void launch_update(const Launch &L, long long count, Work<T> &w, int mode);
+// out[s] = (Tout)(scale * f[i] * in[s]) for every entry s of row i
+template <class Tin, class Tout>
+void launch_row_scale(const Launch &L, int n, const int *Pp, int lanes, const double *f,
+                      double scale, const Tin *in, Tout *out);
 void launch_state_reset(const Launch &L, DevState *st);
 void set_iter_attributes();
+int staged_blocks_per_sm();
 void set_adjoint_attributes();
 void launch_state_begin(const Launch &L, DevState *st, double tau);
 

@@ -238,51 +238,378 @@ k_project_warp(int n, int k, const int *__restrict__ Pp, const int *__restrict__
 }
 
 // ---------------------------------------------------------------------------
-// Direction update of Algorithm 3 with the Jacobi preconditioner:
-// y = z + beta y with z = M_J^{-1} r = r / A(i,i) row by row (beta = 0 before
-// the first step).  G lanes per row of P.  The projection after M^{-1} is
-// skipped: by Theorem 1 and its corollary the row scaling keeps r in
-// range(Pi_B).
+// k = 1 masked product on the SELL-32 plan: one warp per slice of 32 rows,
+// one lane per row.  Step j loads entry j of the 32 rows (a^_il, the offset
+// of row l of Y, the slot map) as three contiguous 128/64-byte runs, then
+// gathers y_lq for every slot s of row i that row l holds; one FMA per
+// in-pattern product.  Epilogue per row: x -= q (q^T x), store, y^T y_.
 // ---------------------------------------------------------------------------
-template <class T, int G>
+template <class T>
+__device__ __forceinline__ void sell_step(T a, int off, unsigned int im, const T *__restrict__ Y,
+                                          T &a0, T &a1, T &a2, T &a3) {
+    const unsigned int q0 = im & 7u, q1 = (im >> 3) & 7u, q2 = (im >> 6) & 7u, q3 = (im >> 9) & 7u;
+    if (q0 < 4u) a0 = fmat(a, Y[off + q0], a0);
+    if (q1 < 4u) a1 = fmat(a, Y[off + q1], a1);
+    if (q2 < 4u) a2 = fmat(a, Y[off + q2], a2);
+    if (q3 < 4u) a3 = fmat(a, Y[off + q3], a3);
+}
+
+// The first 8 entries of every row are loaded in one round (three coalesced
+// runs per entry) before any gather of Y is issued, so that a slice costs
+// two memory round trips; longer rows continue in a loop.
+template <class T>
 __global__ void __launch_bounds__(kBlock)
-k_ydir(int n, const int *__restrict__ Pp, const T *__restrict__ dinv, const T *__restrict__ R,
-       T *__restrict__ Y, const DevState *st) {
-    if (st->stop) return;
-    const T beta = (T)st->beta;
-    const int gid = blockIdx.x * blockDim.x + threadIdx.x;
-    const int sub = gid % G, groups = gridDim.x * blockDim.x / G;
-    for (int i = gid / G; i < n; i += groups) {
-        const int p0 = Pp[i], p1 = Pp[i + 1];
-        const T d = dinv[i];
-        for (int s = p0 + sub; s < p1; s += G) Y[s] = fmat(d, R[s], beta * Y[s]);
+k_kprod_k1_sell(int n, const int *__restrict__ sell_ptr, const T *__restrict__ sa,
+                const int *__restrict__ soff, const unsigned short *__restrict__ smap,
+                const int *__restrict__ Pp, const T *__restrict__ qv, const T *__restrict__ Y,
+                T *__restrict__ out, int project, int dot_mode, DevState *st, double *partials,
+                double *hist, int cap, int check_stop) {
+    if (check_stop && st->stop) return;
+    constexpr int U = 8;
+    const int lane = threadIdx.x & 31;
+    const int warp = (blockIdx.x * blockDim.x + threadIdx.x) >> 5;
+    const int nwarps = (gridDim.x * blockDim.x) >> 5;
+    const int nslices = (n + 31) >> 5;
+    Dot<T> dot;
+    // slice pointers and row pointers of the next slice are fetched one
+    // iteration ahead
+    int sl = warp;
+    int nb0 = 0, nb1 = 0, np0 = 0, np1 = 0;
+    if (sl < nslices) {
+        nb0 = sell_ptr[sl];
+        nb1 = sell_ptr[sl + 1];
+        const int i = sl * 32 + lane;
+        if (i < n) {
+            np0 = Pp[i];
+            np1 = Pp[i + 1];
+        }
+    }
+    for (; sl < nslices; sl += nwarps) {
+        const int base = nb0, len = (nb1 - nb0) >> 5, p0 = np0, m = np1 - np0;
+        const T *pa = sa + base + lane;
+        const int *po = soff + base + lane;
+        const unsigned short *pm = smap + base + lane;
+        T av[U];
+        int ov[U];
+        unsigned int mv[U];
+#pragma unroll
+        for (int j = 0; j < U; ++j) {
+            if (j < len) {
+                av[j] = __ldcs(pa + j * 32);
+                ov[j] = __ldcs(po + j * 32);
+                mv[j] = __ldcs(pm + j * 32);
+            } else {
+                av[j] = T(0);
+                ov[j] = 0;
+                mv[j] = 0xFFFu;
+            }
+        }
+        const int nsl = sl + nwarps;
+        if (nsl < nslices) {
+            nb0 = sell_ptr[nsl];
+            nb1 = sell_ptr[nsl + 1];
+            const int ni = nsl * 32 + lane;
+            if (ni < n) {
+                np0 = Pp[ni];
+                np1 = Pp[ni + 1];
+            } else {
+                np0 = np1 = 0;
+            }
+        }
+        // the row's own values (projection vector, y for the dot) meanwhile
+        T q[4], yown[4];
+#pragma unroll
+        for (int s = 0; s < 4; ++s) {
+            const bool h = s < m;
+            q[s] = (h && project) ? __ldcs(qv + p0 + s) : T(0);
+            yown[s] = (h && dot_mode) ? Y[p0 + s] : T(0);
+        }
+        T a0 = T(0), a1 = T(0), a2 = T(0), a3 = T(0);
+#pragma unroll
+        for (int j = 0; j < U; ++j) sell_step(av[j], ov[j], mv[j], Y, a0, a1, a2, a3);
+        for (int j = U; j < len; ++j)
+            sell_step(__ldcs(pa + j * 32), __ldcs(po + j * 32), (unsigned int)__ldcs(pm + j * 32), Y,
+                      a0, a1, a2, a3);
+        T x[4] = {a0, a1, a2, a3};
+        if (project) {
+            T t = T(0);
+#pragma unroll
+            for (int s = 0; s < 4; ++s) t = fmat(q[s], x[s], t);
+#pragma unroll
+            for (int s = 0; s < 4; ++s) x[s] = fmat(-q[s], t, x[s]);
+        }
+#pragma unroll
+        for (int s = 0; s < 4; ++s)
+            if (s < m) {
+                out[p0 + s] = x[s];
+                if (dot_mode) dot.add(yown[s], x[s]);
+            }
+    }
+    if (dot_mode) {
+        __shared__ double sh[32];
+        double bt = block_dot_total(dot, sh);
+        double total;
+        if (grid_reduce(bt, partials, &st->ticket[0], &total)) {
+            if (dot_mode == DOT_ALPHA) finalize_alpha(st, total, hist, cap);
+            else st->aux = total;
+        }
     }
 }
 
-// Vector updates dW += alpha y, r -= alpha y_ (UPD_STEP), then
-// gamma = r^T M_J^{-1} r; UPD_INIT only forms gamma, UPD_FLOOR sets the
-// convergence floor from the (unprojected) r.
-template <class T, int G>
+// ---------------------------------------------------------------------------
+// The same product (float) with the plan staged through shared memory.
+// A block owns groups of 8 consecutive slices (one warp per slice); the plan
+// of a group is one contiguous run of the three SELL arrays, copied with
+// 16-byte cp.async into one of two shared buffers while the block works on
+// the previous group, so the only memory latency left in a slice is the
+// gather of Y.  A group whose plan exceeds the buffer (rows longer than 8)
+// is read from global memory directly.
+// ---------------------------------------------------------------------------
+__device__ __forceinline__ void cp_async16(void *smem, const void *gmem) {
+    const unsigned int s = (unsigned int)__cvta_generic_to_shared(smem);
+    asm volatile("cp.async.cg.shared.global [%0], [%1], 16;\n" ::"r"(s), "l"(gmem) : "memory");
+}
+__device__ __forceinline__ void cp_async_commit() { asm volatile("cp.async.commit_group;\n" ::: "memory"); }
+__device__ __forceinline__ void cp_async_wait1() { asm volatile("cp.async.wait_group 1;\n" ::: "memory"); }
+__device__ __forceinline__ void cp_async_wait0() { asm volatile("cp.async.wait_group 0;\n" ::: "memory"); }
+
+constexpr int kStageWarps = kBlock / 32;
+constexpr int kStageCap = kStageWarps * 8 * 32;  // plan entries per buffer
+
 __global__ void __launch_bounds__(kBlock)
-k_update(int n, const int *__restrict__ Pp, const T *__restrict__ dinv, T *__restrict__ R,
-         const T *__restrict__ Y, const T *__restrict__ Yb, T *__restrict__ X, DevState *st,
-         double *partials, int mode) {
+k_kprod_k1_staged(int n, const int *__restrict__ sell_ptr, const float *__restrict__ sa,
+                  const int *__restrict__ soff, const unsigned short *__restrict__ smap,
+                  const int *__restrict__ Pp, const float *__restrict__ qv,
+                  const float *__restrict__ Y, float *__restrict__ out, int project, int dot_mode,
+                  DevState *st, double *partials, double *hist, int cap, int check_stop) {
+    if (check_stop && st->stop) return;
+    __shared__ __align__(16) float sA[2][kStageCap];
+    __shared__ __align__(16) int sO[2][kStageCap];
+    __shared__ __align__(16) unsigned short sM[2][kStageCap];
+    __shared__ int sPtr[2][kStageWarps + 1];
+    __shared__ int sFit[2];
+    const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+    const int nslices = (n + 31) >> 5;
+    const int ngroups = (nslices + kStageWarps - 1) / kStageWarps;
+
+    // issue the copies of group g into buffer b (always commits one group)
+    auto prefetch = [&](int g, int b) {
+        const int s0 = g * kStageWarps, s1 = min(s0 + kStageWarps, nslices);
+        const int pb = sell_ptr[s0], pe = sell_ptr[s1];
+        const int cnt = pe - pb;  // a multiple of 32
+        if (threadIdx.x <= kStageWarps) sPtr[b][threadIdx.x] = sell_ptr[min(s0 + (int)threadIdx.x, s1)];
+        const bool fit = cnt <= kStageCap;
+        if (threadIdx.x == 0) sFit[b] = fit ? 1 : 0;
+        if (fit) {
+            for (int c = threadIdx.x; c < cnt / 4; c += blockDim.x) {
+                cp_async16(&sA[b][4 * c], sa + pb + 4 * c);
+                cp_async16(&sO[b][4 * c], soff + pb + 4 * c);
+            }
+            for (int c = threadIdx.x; c < cnt / 8; c += blockDim.x)
+                cp_async16(&sM[b][8 * c], smap + pb + 8 * c);
+        }
+        cp_async_commit();
+    };
+
+    Dot<float> dot;
+    int b = 0;
+    if ((int)blockIdx.x < ngroups) prefetch(blockIdx.x, 0);
+    else cp_async_commit();
+    for (int g = blockIdx.x; g < ngroups; g += gridDim.x, b ^= 1) {
+        const int gn = g + gridDim.x;
+        if (gn < ngroups) prefetch(gn, b ^ 1);
+        else cp_async_commit();
+        const int sl = g * kStageWarps + warp;
+        const bool have = sl < nslices;
+        const int i = sl * 32 + lane;
+        const bool valid = have && i < n;
+        int p0 = 0, m = 0;
+        if (valid) {
+            p0 = Pp[i];
+            m = Pp[i + 1] - p0;
+        }
+        float q[4], yown[4];
+#pragma unroll
+        for (int s = 0; s < 4; ++s) {
+            const bool h = s < m;
+            q[s] = (h && project) ? __ldcs(qv + p0 + s) : 0.f;
+            yown[s] = (h && dot_mode) ? Y[p0 + s] : 0.f;
+        }
+        cp_async_wait1();
+        __syncthreads();
+        if (have) {
+            const int gb = sPtr[b][warp];
+            const int len = (sPtr[b][warp + 1] - gb) >> 5;
+            const int lb = gb - sPtr[b][0];
+            const bool fit = sFit[b] != 0;
+            float a0 = 0.f, a1 = 0.f, a2 = 0.f, a3 = 0.f;
+            if (fit) {
+                float av[8];
+                int ov[8];
+                unsigned int mv[8];
+#pragma unroll
+                for (int j = 0; j < 8; ++j) {
+                    if (j < len) {
+                        av[j] = sA[b][lb + j * 32 + lane];
+                        ov[j] = sO[b][lb + j * 32 + lane];
+                        mv[j] = sM[b][lb + j * 32 + lane];
+                    } else {
+                        av[j] = 0.f;
+                        ov[j] = 0;
+                        mv[j] = 0xFFFu;
+                    }
+                }
+#pragma unroll
+                for (int j = 0; j < 8; ++j) sell_step(av[j], ov[j], mv[j], Y, a0, a1, a2, a3);
+            } else {
+                for (int j = 0; j < len; ++j)
+                    sell_step(__ldcs(sa + gb + j * 32 + lane), __ldcs(soff + gb + j * 32 + lane),
+                              (unsigned int)__ldcs(smap + gb + j * 32 + lane), Y, a0, a1, a2, a3);
+            }
+            float x[4] = {a0, a1, a2, a3};
+            if (project) {
+                float t = 0.f;
+#pragma unroll
+                for (int s = 0; s < 4; ++s) t = fmaf(q[s], x[s], t);
+#pragma unroll
+                for (int s = 0; s < 4; ++s) x[s] = fmaf(-q[s], t, x[s]);
+            }
+#pragma unroll
+            for (int s = 0; s < 4; ++s)
+                if (s < m) {
+                    out[p0 + s] = x[s];
+                    if (dot_mode) dot.add(yown[s], x[s]);
+                }
+        }
+        __syncthreads();  // buffer b is refilled two groups later
+    }
+    cp_async_wait0();
+    if (dot_mode) {
+        __shared__ double sh[32];
+        double bt = block_dot_total(dot, sh);
+        double total;
+        if (grid_reduce(bt, partials, &st->ticket[0], &total)) {
+            if (dot_mode == DOT_ALPHA) finalize_alpha(st, total, hist, cap);
+            else st->aux = total;
+        }
+    }
+}
+
+// k = 1 stand-alone x = scale * (x - q (q^T x)), one thread per row.
+template <class T>
+__global__ void __launch_bounds__(kBlock)
+k_project_k1(int n, const int *__restrict__ Pp, const T *__restrict__ qv, T *x, T scale) {
+    for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < n; i += gridDim.x * blockDim.x) {
+        const int p0 = Pp[i], p1 = Pp[i + 1];
+        T t = T(0);
+        for (int s = p0; s < p1; ++s) t = fmat(qv[s], x[s], t);
+        for (int s = p0; s < p1; ++s) x[s] = scale * fmat(-qv[s], t, x[s]);
+    }
+}
+
+// ---------------------------------------------------------------------------
+// Vector steps of Algorithm 3 in the symmetrically scaled variables
+// r~ = D^{-1/2} r, y~ = D^{1/2} y, dW~ = D^{1/2} dW (Jacobi M = D, Theorem 1):
+// z = M^{-1} r becomes D^{-1/2} r~, so y = z + beta y is y~ = r~ + beta y~ and
+// gamma = r^T M^{-1} r = <r~, r~>.  Every step is then a flat stream over the
+// value arrays, 16-byte vectorised.
+// ---------------------------------------------------------------------------
+template <class T>
+struct Vec;
+template <>
+struct Vec<float> {
+    using V = float4;
+    static constexpr int W = 4;
+};
+template <>
+struct Vec<double> {
+    using V = double2;
+    static constexpr int W = 2;
+};
+
+__device__ __forceinline__ float4 axpy4(float b, float4 y, float4 r) {
+    return make_float4(fmaf(b, y.x, r.x), fmaf(b, y.y, r.y), fmaf(b, y.z, r.z), fmaf(b, y.w, r.w));
+}
+__device__ __forceinline__ double2 axpy4(double b, double2 y, double2 r) {
+    return make_double2(fma(b, y.x, r.x), fma(b, y.y, r.y));
+}
+
+// y~ = r~ + beta y~
+template <class T>
+__global__ void __launch_bounds__(kBlock)
+k_ydir_flat(long long count, const T *__restrict__ R, T *__restrict__ Y, const DevState *st) {
+    if (st->stop) return;
+    const T beta = (T)st->beta;
+    using V = typename Vec<T>::V;
+    constexpr int W = Vec<T>::W;
+    const long long nv = count / W;
+    const long long stride = (long long)gridDim.x * blockDim.x;
+    const V *R4 = reinterpret_cast<const V *>(R);
+    V *Y4 = reinterpret_cast<V *>(Y);
+    for (long long v = blockIdx.x * (long long)blockDim.x + threadIdx.x; v < nv; v += stride)
+        Y4[v] = axpy4(beta, Y4[v], R4[v]);
+    for (long long q = nv * W + blockIdx.x * (long long)blockDim.x + threadIdx.x; q < count;
+         q += stride)
+        Y[q] = fmat(beta, Y[q], R[q]);
+}
+
+// dW~ += alpha y~, r~ -= alpha y_~ (UPD_STEP), then gamma = <r~, r~>;
+// UPD_INIT only forms gamma; UPD_FLOOR sets the convergence floor.
+template <class T>
+__device__ __forceinline__ void upd1(T &r, T &x, T y, T yb, T alpha, int mode, Dot<T> &dot) {
+    if (mode == UPD_STEP) {
+        x = fmat(alpha, y, x);
+        r = fmat(-alpha, yb, r);
+    }
+    dot.add(r, r);
+}
+
+template <class T>
+__global__ void __launch_bounds__(kBlock)
+k_update_flat(long long count, T *__restrict__ R, const T *__restrict__ Y,
+              const T *__restrict__ Yb, T *__restrict__ X, DevState *st, double *partials,
+              int mode) {
     if (mode != UPD_FLOOR && st->stop) return;
     const T alpha = (T)st->alpha;
+    using V = typename Vec<T>::V;
+    constexpr int W = Vec<T>::W;
+    const long long nv = count / W;
+    const long long stride = (long long)gridDim.x * blockDim.x;
     Dot<T> dot;
-    const int gid = blockIdx.x * blockDim.x + threadIdx.x;
-    const int sub = gid % G, groups = gridDim.x * blockDim.x / G;
-    for (int i = gid / G; i < n; i += groups) {
-        const int p0 = Pp[i], p1 = Pp[i + 1];
-        const T d = dinv[i];
-        for (int s = p0 + sub; s < p1; s += G) {
-            T r = R[s];
-            if (mode == UPD_STEP) {
-                X[s] = fmat(alpha, Y[s], X[s]);
-                r = fmat(-alpha, Yb[s], r);
-                R[s] = r;
+    const bool step = (mode == UPD_STEP);
+    for (long long v = blockIdx.x * (long long)blockDim.x + threadIdx.x; v < nv; v += stride) {
+        V r = reinterpret_cast<V *>(R)[v];
+        if (step) {
+            V x = reinterpret_cast<V *>(X)[v];
+            const V y = reinterpret_cast<const V *>(Y)[v];
+            const V yb = reinterpret_cast<const V *>(Yb)[v];
+            upd1(r.x, x.x, y.x, yb.x, alpha, mode, dot);
+            upd1(r.y, x.y, y.y, yb.y, alpha, mode, dot);
+            if constexpr (W == 4) {
+                upd1(r.z, x.z, y.z, yb.z, alpha, mode, dot);
+                upd1(r.w, x.w, y.w, yb.w, alpha, mode, dot);
             }
-            dot.add(r, d * r);
+            reinterpret_cast<V *>(X)[v] = x;
+            reinterpret_cast<V *>(R)[v] = r;
+        } else {
+            dot.add(r.x, r.x);
+            dot.add(r.y, r.y);
+            if constexpr (W == 4) {
+                dot.add(r.z, r.z);
+                dot.add(r.w, r.w);
+            }
+        }
+    }
+    for (long long q = nv * W + blockIdx.x * (long long)blockDim.x + threadIdx.x; q < count;
+         q += stride) {
+        T r = R[q];
+        if (step) {
+            T x = X[q];
+            upd1(r, x, Y[q], Yb[q], alpha, mode, dot);
+            X[q] = x;
+            R[q] = r;
+        } else {
+            dot.add(r, r);
         }
     }
     __shared__ double sh[32];
@@ -290,6 +617,19 @@ k_update(int n, const int *__restrict__ Pp, const T *__restrict__ dinv, T *__res
     double total;
     if (grid_reduce(bt, partials, &st->ticket[1], &total))
         finalize_gamma(st, total, mode, GammaFloor<T>::value);
+}
+
+// out[s] = (Tout)(scale * f[i] * in[s]) on the entries of row i (G lanes per row)
+template <class Tin, class Tout, int G>
+__global__ void __launch_bounds__(kBlock)
+k_row_scale(int n, const int *__restrict__ Pp, const double *__restrict__ f, double scale,
+            const Tin *in, Tout *out) {
+    const int gid = blockIdx.x * blockDim.x + threadIdx.x;
+    const int sub = gid % G, groups = gridDim.x * blockDim.x / G;
+    for (int i = gid / G; i < n; i += groups) {
+        const double fi = scale * f[i];
+        for (int s = Pp[i] + sub; s < Pp[i + 1]; s += G) out[s] = (Tout)(fi * (double)in[s]);
+    }
 }
 
 __global__ void k_state_reset(DevState *st) {
@@ -311,14 +651,30 @@ template <class T>
 void launch_kprod(const Launch &L, const Ops<T> &o, const T *Y, T *out, int project, int dot_mode,
                   Work<T> &w, int check_stop) {
     if (o.n <= 0) return;
-    if (o.k == 1 && o.maxrow <= 4) {
+    if (o.k == 1 && o.sell_ptr && o.sa && o.qv && o.maxrow <= 4) {
+        if constexpr (sizeof(T) == 4) {
+            // one block per group of 8 slices, at most the resident grid
+            const long long groups = ((o.n + 31) / 32 + kStageWarps - 1) / kStageWarps;
+            const int g = (int)(groups < L.grid_staged ? groups : L.grid_staged);
+            k_kprod_k1_staged<<<g, kBlock, 0, L.stream>>>(o.n, o.sell_ptr, o.sa, o.soff, o.smap,
+                                                          o.Pp, o.qv, Y, out, project, dot_mode,
+                                                          w.st, w.partials, w.hist, w.hist_cap,
+                                                          check_stop);
+        } else {
+            const int g = grid_for((long long)((o.n + 31) / 32) * 32, L.grid_rows);
+            k_kprod_k1_sell<T><<<g, kBlock, 0, L.stream>>>(o.n, o.sell_ptr, o.sa, o.soff, o.smap,
+                                                            o.Pp, o.qv, Y, out, project, dot_mode,
+                                                            w.st, w.partials, w.hist, w.hist_cap,
+                                                            check_stop);
+        }
+    } else if (o.k == 1 && o.maxrow <= 4) {
         k_kprod_row_k1<T, 4><<<grid_for(o.n, L.grid_rows), kBlock, 0, L.stream>>>(
             o.n, o.Ap, o.Aj, o.Av, o.Pp, o.Pj, Y, out, o.Bc, o.Ginv, project, dot_mode, w.st,
-            w.partials, w.hist, w.hist_cap, check_stop); note_launch();
+            w.partials, w.hist, w.hist_cap, check_stop);
     } else if (o.k == 1 && o.maxrow <= 8) {
         k_kprod_row_k1<T, 8><<<grid_for(o.n, L.grid_rows), kBlock, 0, L.stream>>>(
             o.n, o.Ap, o.Aj, o.Av, o.Pp, o.Pj, Y, out, o.Bc, o.Ginv, project, dot_mode, w.st,
-            w.partials, w.hist, w.hist_cap, check_stop); note_launch();
+            w.partials, w.hist, w.hist_cap, check_stop);
     } else {
         const int mcap = staging_cap(o.maxrow);
         const size_t smem = (size_t)(kBlock / 32) * mcap * (sizeof(T) + sizeof(int));
@@ -326,39 +682,61 @@ void launch_kprod(const Launch &L, const Ops<T> &o, const T *Y, T *out, int proj
         k_kprod_warp<T><<<g, kBlock, smem, L.stream>>>(o.n, o.k, o.Ap, o.Aj, o.Av, o.Pp, o.Pj, Y,
                                                        out, o.Bc, o.Ginv, project, dot_mode, w.st,
                                                        w.partials, w.hist, w.hist_cap, check_stop,
-                                                       mcap); note_launch();
+                                                       mcap);
     }
+    note_launch();
 }
 
 template <class T>
 void launch_project(const Launch &L, const Ops<T> &o, T *x, T scale) {
     if (o.n <= 0) return;
-    k_project_warp<T><<<grid_for((long long)o.n * 32, L.grid_rows), kBlock, 0, L.stream>>>(
-        o.n, o.k, o.Pp, o.Pj, o.Bc, o.Ginv, x, scale); note_launch();
-}
-
-template <class T>
-void launch_ydir(const Launch &L, const Ops<T> &o, Work<T> &w) {
-    if (o.n <= 0) return;
-    if (o.lanes == 1)
-        k_ydir<T, 1><<<grid_for(o.n, L.grid_rows), kBlock, 0, L.stream>>>(o.n, o.Pp, o.dinv, w.R,
-                                                                         w.Y, w.st);
+    if (o.k == 1 && o.qv)
+        k_project_k1<T><<<grid_for(o.n, L.grid_rows), kBlock, 0, L.stream>>>(o.n, o.Pp, o.qv, x,
+                                                                             scale);
     else
-        k_ydir<T, 32><<<grid_for((long long)o.n * 32, L.grid_rows), kBlock, 0, L.stream>>>(
-            o.n, o.Pp, o.dinv, w.R, w.Y, w.st);
+        k_project_warp<T><<<grid_for((long long)o.n * 32, L.grid_rows), kBlock, 0, L.stream>>>(
+            o.n, o.k, o.Pp, o.Pj, o.Bc, o.Ginv, x, scale);
     note_launch();
 }
 
 template <class T>
-void launch_update(const Launch &L, const Ops<T> &o, Work<T> &w, int mode) {
-    if (o.n <= 0) return;
-    if (o.lanes == 1)
-        k_update<T, 1><<<grid_for(o.n, L.grid_rows), kBlock, 0, L.stream>>>(
-            o.n, o.Pp, o.dinv, w.R, w.Y, w.Yb, w.X, w.st, w.partials, mode);
-    else
-        k_update<T, 32><<<grid_for((long long)o.n * 32, L.grid_rows), kBlock, 0, L.stream>>>(
-            o.n, o.Pp, o.dinv, w.R, w.Y, w.Yb, w.X, w.st, w.partials, mode);
+void launch_ydir(const Launch &L, long long count, Work<T> &w) {
+    if (count <= 0) return;
+    const int g = grid_for((count + Vec<T>::W - 1) / Vec<T>::W, L.grid_rows);
+    k_ydir_flat<T><<<g, kBlock, 0, L.stream>>>(count, w.R, w.Y, w.st);
     note_launch();
+}
+
+template <class T>
+void launch_update(const Launch &L, long long count, Work<T> &w, int mode) {
+    if (count <= 0) return;
+    const int g = grid_for((count + Vec<T>::W - 1) / Vec<T>::W, L.grid_rows);
+    k_update_flat<T><<<g, kBlock, 0, L.stream>>>(count, w.R, w.Y, w.Yb, w.X, w.st, w.partials,
+                                                  mode);
+    note_launch();
+}
+
+template <class Tin, class Tout>
+void launch_row_scale(const Launch &L, int n, const int *Pp, int lanes, const double *f,
+                      double scale, const Tin *in, Tout *out) {
+    if (n <= 0) return;
+    if (lanes == 1)
+        k_row_scale<Tin, Tout, 1><<<grid_for(n, L.grid_rows), kBlock, 0, L.stream>>>(
+            n, Pp, f, scale, in, out);
+    else
+        k_row_scale<Tin, Tout, 32><<<grid_for((long long)n * 32, L.grid_rows), kBlock, 0,
+                                      L.stream>>>(n, Pp, f, scale, in, out);
+    note_launch();
+}
+
+int staged_blocks_per_sm() {
+    int nb = 0;
+    if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&nb, k_kprod_k1_staged, kBlock, 0) !=
+        cudaSuccess) {
+        cudaGetLastError();
+        nb = 1;
+    }
+    return nb > 0 ? nb : 1;
 }
 
 void set_iter_attributes() {
@@ -367,10 +745,14 @@ void set_iter_attributes() {
     cudaFuncSetAttribute(k_kprod_warp<float>, cudaFuncAttributeMaxDynamicSharedMemorySize, bytes);
 }
 
-void launch_state_reset(const Launch &L, DevState *st) { k_state_reset<<<1, 1, 0, L.stream>>>(st); note_launch(); }
+void launch_state_reset(const Launch &L, DevState *st) {
+    k_state_reset<<<1, 1, 0, L.stream>>>(st);
+    note_launch();
+}
 
 void launch_state_begin(const Launch &L, DevState *st, double tau) {
-    k_state_begin<<<1, 1, 0, L.stream>>>(st, tau); note_launch();
+    k_state_begin<<<1, 1, 0, L.stream>>>(st, tau);
+    note_launch();
 }
 
 template void launch_kprod<double>(const Launch &, const Ops<double> &, const double *, double *,
@@ -379,9 +761,15 @@ template void launch_kprod<float>(const Launch &, const Ops<float> &, const floa
                                   int, Work<float> &, int);
 template void launch_project<double>(const Launch &, const Ops<double> &, double *, double);
 template void launch_project<float>(const Launch &, const Ops<float> &, float *, float);
-template void launch_ydir<double>(const Launch &, const Ops<double> &, Work<double> &);
-template void launch_ydir<float>(const Launch &, const Ops<float> &, Work<float> &);
-template void launch_update<double>(const Launch &, const Ops<double> &, Work<double> &, int);
-template void launch_update<float>(const Launch &, const Ops<float> &, Work<float> &, int);
+template void launch_ydir<double>(const Launch &, long long, Work<double> &);
+template void launch_ydir<float>(const Launch &, long long, Work<float> &);
+template void launch_update<double>(const Launch &, long long, Work<double> &, int);
+template void launch_update<float>(const Launch &, long long, Work<float> &, int);
+template void launch_row_scale<double, double>(const Launch &, int, const int *, int,
+                                               const double *, double, const double *, double *);
+template void launch_row_scale<double, float>(const Launch &, int, const int *, int,
+                                              const double *, double, const double *, float *);
+template void launch_row_scale<float, double>(const Launch &, int, const int *, int,
+                                              const double *, double, const float *, double *);
 
 }  // namespace emin

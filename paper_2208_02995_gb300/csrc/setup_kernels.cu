@@ -223,45 +223,299 @@ __global__ void k_gram(int n, const int *__restrict__ Pp, const int *__restrict_
 }
 
 // Least-norm constraint correction of one row (Algorithm 2, Eq. (resEq)):
-//   p = base + add;  r = B(i,:)^T - B_i^T p;  p += B_i G_i^{-1} r.
+//   p = base + f_i add;  r = B(i,:)^T - B_i^T p;  p += B_i G_i^{-1} r.
+// With correct == 0 only p = base + f_i add is formed.
 template <int K>
 __global__ void k_restore(int n, const int *__restrict__ Pp, const int *__restrict__ Pj,
                           const double *__restrict__ Bc, const double *__restrict__ B,
                           const double *__restrict__ Ginv, const double *base,
                           const double *__restrict__ add64, const float *__restrict__ add32,
-                          double *P) {
+                          const double *__restrict__ f, int correct, double *P) {
     constexpr int KK = K * (K + 1) / 2;
     for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < n; i += gridDim.x * blockDim.x) {
         const int p0 = Pp[i], p1 = Pp[i + 1];
-        double r[K];
-#pragma unroll
-        for (int a = 0; a < K; ++a) r[a] = B[(size_t)i * K + a];
-        for (int s = p0; s < p1; ++s) {
-            double p = base[s];
-            if (add64) p += add64[s];
-            if (add32) p += (double)add32[s];
-            const double *b = Bc + (size_t)Pj[s] * K;
-#pragma unroll
-            for (int a = 0; a < K; ++a) r[a] = fma(-b[a], p, r[a]);
-        }
+        const double fi = f ? f[i] : 1.0;
         double c[K];
-        const double *g = Ginv + (size_t)i * KK;
 #pragma unroll
-        for (int a = 0; a < K; ++a) {
-            double v = 0.0;
+        for (int a = 0; a < K; ++a) c[a] = 0.0;
+        if (correct) {
+            double r[K];
 #pragma unroll
-            for (int b = 0; b < K; ++b) v = fma(g[a >= b ? tri(a, b) : tri(b, a)], r[b], v);
-            c[a] = v;
+            for (int a = 0; a < K; ++a) r[a] = B[(size_t)i * K + a];
+            for (int s = p0; s < p1; ++s) {
+                double p = base[s];
+                if (add64) p = fma(fi, add64[s], p);
+                if (add32) p = fma(fi, (double)add32[s], p);
+                const double *b = Bc + (size_t)Pj[s] * K;
+#pragma unroll
+                for (int a = 0; a < K; ++a) r[a] = fma(-b[a], p, r[a]);
+            }
+            const double *g = Ginv + (size_t)i * KK;
+#pragma unroll
+            for (int a = 0; a < K; ++a) {
+                double v = 0.0;
+#pragma unroll
+                for (int b = 0; b < K; ++b) v = fma(g[a >= b ? tri(a, b) : tri(b, a)], r[b], v);
+                c[a] = v;
+            }
         }
         for (int s = p0; s < p1; ++s) {
             double p = base[s];
-            if (add64) p += add64[s];
-            if (add32) p += (double)add32[s];
-            const double *b = Bc + (size_t)Pj[s] * K;
+            if (add64) p = fma(fi, add64[s], p);
+            if (add32) p = fma(fi, (double)add32[s], p);
+            if (correct) {
+                const double *b = Bc + (size_t)Pj[s] * K;
 #pragma unroll
-            for (int a = 0; a < K; ++a) p = fma(b[a], c[a], p);
+                for (int a = 0; a < K; ++a) p = fma(b[a], c[a], p);
+            }
             P[s] = p;
         }
+    }
+}
+
+// ---------------------------------------------------------------------------
+// Whole k = 1 set-up of one row (rows of P with at most 4 entries), fused:
+//   Jacobi scaling from d = A(i,i) (Theorem 1: M_J scales row i by 1/d):
+//     D^{-1/2} = s = 1/sqrt(d), D^{1/2} = d s (float on the float path,
+//     double on the FP64 path);
+//   Gram factor of the 1 x m_i block b = Bc(J_i), in double: G = b^T b,
+//     rn = 1/|b| (Newton), G^{-1} = rn^2; projection vector q = b rn in the
+//     iteration type (Pi_B = I - q q^T); G = 0 is rank deficient (error, or
+//     a zero factor under the PINV policy);
+//   least-norm correction of P0 (Algorithm 2), in double:
+//     p += b G^{-1} (B_i - b^T p);
+//   the iteration's start vector x0 = D^{1/2} p in the iteration type.
+// ---------------------------------------------------------------------------
+template <class Tit>
+__global__ void k_setup_k1(int n, const int *__restrict__ dpos, const double *__restrict__ Av,
+                           const int *__restrict__ Pp, const int *__restrict__ Pj,
+                           const double *__restrict__ Bc, const double *__restrict__ B,
+                           const double *__restrict__ P0_in, int policy, int *flags, int *ndef,
+                           double *dsq, double *dhalf, double *Ginv, Tit *qv, double *P0,
+                           Tit *x0) {
+    for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < n; i += gridDim.x * blockDim.x) {
+        const int p0 = Pp[i], m = Pp[i + 1] - p0;
+        double b[4], p[4];
+#pragma unroll
+        for (int s = 0; s < 4; ++s) {
+            const bool h = s < m;
+            b[s] = h ? Bc[Pj[p0 + s]] : 0.0;
+            p[s] = h ? P0_in[p0 + s] : 0.0;
+        }
+        const double Bi = B[i];
+        const int dp = dpos[i];
+        double d = (dp >= 0) ? Av[dp] : 0.0;
+        if (!(d > 0.0) || !isfinite(d)) {
+            atomicOr(flags, F_DIAG);
+            d = 1.0;
+        }
+        // the scaling is a change of variables of the iteration: the float
+        // path takes it in float (exactly representable in double, so every
+        // later use sees the same value), the FP64 path in double
+        double sq, dh;
+        if constexpr (sizeof(Tit) == 4) {
+            const float df = (float)d;
+            const float sf = (df > 0.f && isfinite(df)) ? rsqrtf(df) : 1.f;
+            if (!(df > 0.f) || !isfinite(df)) atomicOr(flags, F_DIAG);
+            sq = (double)sf;
+            dh = (double)(df * sf);
+        } else {
+            sq = rsqrt_newton(d);
+            dh = d * sq;
+        }
+        dsq[i] = sq;
+        dhalf[i] = dh;
+        double G = 0.0;
+#pragma unroll
+        for (int s = 0; s < 4; ++s) G = fma(b[s], b[s], G);
+        double r = 0.0, gi = 0.0;
+        if (G > 0.0) {
+            r = rsqrt_newton(G);
+            gi = r * r;
+        } else if (policy == EMIN_RANK_PINV) {
+            atomicAdd(ndef, 1);
+        } else {
+            atomicOr(flags, F_RANK);
+        }
+        Ginv[i] = gi;
+        double res = Bi;
+#pragma unroll
+        for (int s = 0; s < 4; ++s) res = fma(-b[s], p[s], res);
+        const double c = gi * res;
+#pragma unroll
+        for (int s = 0; s < 4; ++s)
+            if (s < m) {
+                const double pc = fma(b[s], c, p[s]);
+                P0[p0 + s] = pc;
+                if constexpr (sizeof(Tit) == 4) {
+                    x0[p0 + s] = (float)dh * (float)pc;
+                    qv[p0 + s] = (float)b[s] * (float)r;
+                } else {
+                    x0[p0 + s] = dh * pc;
+                    qv[p0 + s] = b[s] * r;
+                }
+            }
+    }
+}
+
+// Final prolongation for k = 1 (rows of P with at most 4 entries):
+// p = P0 + D^{-1/2} dW~ and, when `correct`, the least-norm constraint
+// correction in double p += b G^{-1} (B_i - b^T p) (b = Bc(J_i)).
+template <class Tx>
+__global__ void k_final_k1(int n, const int *__restrict__ Pp, const int *__restrict__ Pj,
+                           const double *__restrict__ Bc, const double *__restrict__ Ginv,
+                           const double *__restrict__ P0, const Tx *__restrict__ X,
+                           const double *__restrict__ dsq, const double *__restrict__ B,
+                           int correct, double *__restrict__ P) {
+    for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < n; i += gridDim.x * blockDim.x) {
+        const int p0 = Pp[i], m = Pp[i + 1] - p0;
+        const double f = dsq[i];
+        double p[4], b[4];
+#pragma unroll
+        for (int s = 0; s < 4; ++s) {
+            const bool h = s < m;
+            p[s] = h ? fma(f, (double)X[p0 + s], P0[p0 + s]) : 0.0;
+            b[s] = (h && correct) ? Bc[Pj[p0 + s]] : 0.0;
+        }
+        if (correct) {
+            double r = B[i];
+#pragma unroll
+            for (int s = 0; s < 4; ++s) r = fma(-b[s], p[s], r);
+            const double c = Ginv[i] * r;
+#pragma unroll
+            for (int s = 0; s < 4; ++s) p[s] = fma(b[s], c, p[s]);
+        }
+#pragma unroll
+        for (int s = 0; s < 4; ++s)
+            if (s < m) P[p0 + s] = p[s];
+    }
+}
+
+// Longest row of A in every slice of 32 rows.
+__global__ void k_sell_len(int n, const int *__restrict__ Ap, int *slen) {
+    const int ns = (n + 31) / 32;
+    for (int sl = blockIdx.x * blockDim.x + threadIdx.x; sl < ns; sl += gridDim.x * blockDim.x) {
+        int mx = 0;
+        for (int i = sl * 32; i < min(n, sl * 32 + 32); ++i) mx = max(mx, Ap[i + 1] - Ap[i]);
+        slen[sl] = mx;
+    }
+}
+
+// The k = 1 plan of the fixed pattern (the adjacency of Section 4, built
+// once) in SELL-32 order: for every stored (i, l) of A, the offset of row l
+// of P and, for each slot s < 4 of row i, the position q of the same column
+// in row l (3 bits, 7 if absent).  Padding entries carry no slot (map 0xFFF)
+// and offset 0.  Requires rows of P with at most 4 entries.
+__global__ void k_sell_plan(int n, const int *__restrict__ Ap, const int *__restrict__ Aj,
+                            const int *__restrict__ Pp, const int *__restrict__ Pj,
+                            const int *__restrict__ sell_ptr, int *soff, unsigned short *smap,
+                            int *dpos) {
+    for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < n; i += gridDim.x * blockDim.x) {
+        const int sl = i >> 5, lane = i & 31;
+        const int base = sell_ptr[sl], len = (sell_ptr[sl + 1] - base) >> 5;
+        const int p0 = Pp[i], m = Pp[i + 1] - p0, e0 = Ap[i], rl = Ap[i + 1] - e0;
+        int J[4];
+#pragma unroll
+        for (int s = 0; s < 4; ++s) J[s] = (s < m) ? Pj[p0 + s] : -1;
+        int dp = -1;
+        for (int j = 0; j < rl; ++j)
+            if (Aj[e0 + j] == i) dp = e0 + j;
+        dpos[i] = dp;  // position of A(i,i) in the CSR arrays (-1: missing)
+        for (int j = 0; j < len; ++j) {
+            const int pos = base + j * 32 + lane;
+            unsigned int map = 0xFFFu;
+            int off = 0;
+            if (j < rl) {
+                const int l = Aj[e0 + j];
+                const int q0 = Pp[l], ml = Pp[l + 1] - q0;
+                for (int q = 0; q < ml && q < 4; ++q) {
+                    const int c = Pj[q0 + q];
+#pragma unroll
+                    for (int s = 0; s < 4; ++s)
+                        if (c == J[s]) map = (map & ~(7u << (3 * s))) | ((unsigned)q << (3 * s));
+                }
+                off = q0;
+            }
+            soff[pos] = off;
+            smap[pos] = (unsigned short)map;
+        }
+    }
+}
+
+// A^ = D^{-1/2} A D^{-1/2} in SELL-32 order (padding 0).  One warp per
+// slice: the slice's CSR range (contiguous) is read coalesced into shared
+// memory, then each lane writes its row's entries in slice order.
+template <class T>
+__global__ void __launch_bounds__(kBlock)
+k_sell_values(int n, const int *__restrict__ Ap, const int *__restrict__ Aj,
+              const double *__restrict__ Av, const double *__restrict__ dsq,
+              const int *__restrict__ sell_ptr, T *sa) {
+    constexpr int CAP = 256;
+    __shared__ double sv[kBlock / 32][CAP];
+    __shared__ int sc[kBlock / 32][CAP];
+    const int w = threadIdx.x >> 5, lane = threadIdx.x & 31;
+    const int nslices = (n + 31) >> 5;
+    for (int sl = (blockIdx.x * blockDim.x + threadIdx.x) >> 5; sl < nslices;
+         sl += (gridDim.x * blockDim.x) >> 5) {
+        const int i0 = sl * 32, i1 = min(i0 + 32, n);
+        const int eb = Ap[i0], cnt = Ap[i1] - eb;
+        const int base = sell_ptr[sl], len = (sell_ptr[sl + 1] - base) >> 5;
+        const int i = i0 + lane;
+        const bool valid = i < n;
+        const int e0 = valid ? Ap[i] : eb, rl = valid ? Ap[i + 1] - e0 : 0;
+        const double di = valid ? dsq[i] : 0.0;
+        const bool staged = cnt <= CAP;
+        if (staged)
+            for (int t = lane; t < cnt; t += 32) {
+                sv[w][t] = Av[eb + t];
+                sc[w][t] = Aj[eb + t];
+            }
+        __syncwarp();
+        for (int j = 0; j < len; ++j) {
+            T v = T(0);
+            if (j < rl) {
+                const double a = staged ? sv[w][e0 - eb + j] : Av[e0 + j];
+                const int l = staged ? sc[w][e0 - eb + j] : Aj[e0 + j];
+                if constexpr (sizeof(T) == 4)
+                    v = (float)di * (float)a * (float)dsq[l];
+                else
+                    v = di * a * dsq[l];
+            }
+            sa[base + j * 32 + lane] = v;
+        }
+        __syncwarp();
+    }
+}
+
+// Row scales of the symmetric Jacobi scaling: D^{-1/2} and D^{1/2}.
+__global__ void k_diag_scales(int n, const double *__restrict__ dinv, double *dsq, double *dhalf) {
+    for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < n; i += gridDim.x * blockDim.x) {
+        const double s = sqrt(dinv[i]);
+        dsq[i] = s;
+        dhalf[i] = 1.0 / s;
+    }
+}
+
+// A^ = D^{-1/2} A D^{-1/2} (in double, stored as T).
+template <class T>
+__global__ void k_scale_a(int n, const int *__restrict__ Ap, const int *__restrict__ Aj,
+                          const double *__restrict__ Av, const double *__restrict__ dsq, T *Ahat) {
+    for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < n; i += gridDim.x * blockDim.x) {
+        const double di = dsq[i];
+        for (int e = Ap[i]; e < Ap[i + 1]; ++e) Ahat[e] = (T)(di * Av[e] * dsq[Aj[e]]);
+    }
+}
+
+// k = 1: q = b / |b| per row (b = Bc(J_i)), so that Pi_B = I - q q^T.
+template <class T>
+__global__ void k_qvec_k1(int n, const int *__restrict__ Pp, const int *__restrict__ Pj,
+                          const double *__restrict__ Bc, T *qv) {
+    for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < n; i += gridDim.x * blockDim.x) {
+        const int p0 = Pp[i], p1 = Pp[i + 1];
+        double g = 0.0;
+        for (int s = p0; s < p1; ++s) g = fma(Bc[Pj[s]], Bc[Pj[s]], g);
+        const double inv = g > 0.0 ? 1.0 / sqrt(g) : 0.0;
+        for (int s = p0; s < p1; ++s) qv[s] = (T)(Bc[Pj[s]] * inv);
     }
 }
 
@@ -313,13 +567,16 @@ void launch_gram(const Launch &L, int n, int k, const int *Pp, const int *Pj, co
 
 void launch_restore(const Launch &L, int n, int k, const int *Pp, const int *Pj,
                     const double *Bc, const double *B, const double *Ginv, const double *base,
-                    const double *add64, const float *add32, double *P) {
+                    const double *add64, const float *add32, const double *f, int correct,
+                    double *P) {
     if (n <= 0) return;
     const int g = grid_for(n, L.grid_rows);
     switch (k) {
-#define EMIN_RESTORE(KV)                                                                      \
-    case KV:                                                                                  \
-        k_restore<KV><<<g, kBlock, 0, L.stream>>>(n, Pp, Pj, Bc, B, Ginv, base, add64, add32, P); note_launch(); \
+#define EMIN_RESTORE(KV)                                                                   \
+    case KV:                                                                               \
+        k_restore<KV><<<g, kBlock, 0, L.stream>>>(n, Pp, Pj, Bc, B, Ginv, base, add64, add32, \
+                                                  f, correct, P);                          \
+        note_launch();                                                                     \
         break;
         EMIN_RESTORE(1) EMIN_RESTORE(2) EMIN_RESTORE(3) EMIN_RESTORE(4)
         EMIN_RESTORE(5) EMIN_RESTORE(6) EMIN_RESTORE(7) EMIN_RESTORE(8)
@@ -327,6 +584,101 @@ void launch_restore(const Launch &L, int n, int k, const int *Pp, const int *Pj,
         default: break;
     }
 }
+
+template <class Tit>
+void launch_setup_k1(const Launch &L, int n, const int *dpos, const double *Av, const int *Pp,
+                     const int *Pj, const double *Bc, const double *B, const double *P0_in,
+                     int policy, int *flags, int *ndef, double *dsq, double *dhalf, double *Ginv,
+                     Tit *qv, double *P0, Tit *x0) {
+    if (n <= 0) return;
+    k_setup_k1<Tit><<<grid_for(n, L.grid_rows), kBlock, 0, L.stream>>>(
+        n, dpos, Av, Pp, Pj, Bc, B, P0_in, policy, flags, ndef, dsq, dhalf, Ginv, qv, P0, x0);
+    note_launch();
+}
+template void launch_setup_k1<float>(const Launch &, int, const int *, const double *,
+                                     const int *, const int *, const double *, const double *,
+                                     const double *, int, int *, int *, double *, double *,
+                                     double *, float *, double *, float *);
+template void launch_setup_k1<double>(const Launch &, int, const int *, const double *,
+                                      const int *, const int *, const double *, const double *,
+                                      const double *, int, int *, int *, double *, double *,
+                                      double *, double *, double *, double *);
+
+template <class Tx>
+void launch_final_k1(const Launch &L, int n, const int *Pp, const int *Pj, const double *Bc,
+                     const double *Ginv, const double *P0, const Tx *X, const double *dsq,
+                     const double *B, int correct, double *P) {
+    if (n <= 0) return;
+    k_final_k1<Tx><<<grid_for(n, L.grid_rows), kBlock, 0, L.stream>>>(n, Pp, Pj, Bc, Ginv, P0, X,
+                                                                       dsq, B, correct, P);
+    note_launch();
+}
+template void launch_final_k1<float>(const Launch &, int, const int *, const int *,
+                                     const double *, const double *, const double *,
+                                     const float *, const double *, const double *, int,
+                                     double *);
+template void launch_final_k1<double>(const Launch &, int, const int *, const int *,
+                                      const double *, const double *, const double *,
+                                      const double *, const double *, const double *, int,
+                                      double *);
+
+void launch_sell_len(const Launch &L, int n, const int *Ap, int *slen) {
+    if (n <= 0) return;
+    k_sell_len<<<grid_for((n + 31) / 32, L.grid_rows), kBlock, 0, L.stream>>>(n, Ap, slen);
+    note_launch();
+}
+
+void launch_sell_plan(const Launch &L, int n, const int *Ap, const int *Aj, const int *Pp,
+                      const int *Pj, const int *sell_ptr, int *soff, unsigned short *smap,
+                      int *dpos) {
+    if (n <= 0) return;
+    k_sell_plan<<<grid_for(n, L.grid_rows), kBlock, 0, L.stream>>>(n, Ap, Aj, Pp, Pj, sell_ptr,
+                                                                   soff, smap, dpos);
+    note_launch();
+}
+
+template <class T>
+void launch_sell_values(const Launch &L, int n, const int *Ap, const int *Aj, const double *Av,
+                        const double *dsq, const int *sell_ptr, T *sa) {
+    if (n <= 0) return;
+    k_sell_values<T><<<grid_for((long long)((n + 31) / 32) * 32, L.grid_rows), kBlock, 0,
+                       L.stream>>>(n, Ap, Aj, Av, dsq, sell_ptr, sa);
+    note_launch();
+}
+template void launch_sell_values<float>(const Launch &, int, const int *, const int *,
+                                        const double *, const double *, const int *, float *);
+template void launch_sell_values<double>(const Launch &, int, const int *, const int *,
+                                         const double *, const double *, const int *, double *);
+
+void launch_diag_scales(const Launch &L, int n, const double *dinv, double *dsq, double *dhalf) {
+    if (n <= 0) return;
+    k_diag_scales<<<grid_for(n, L.grid_rows), kBlock, 0, L.stream>>>(n, dinv, dsq, dhalf);
+    note_launch();
+}
+
+template <class T>
+void launch_scale_a(const Launch &L, int n, const int *Ap, const int *Aj, const double *Av,
+                    const double *dsq, T *Ahat) {
+    if (n <= 0) return;
+    k_scale_a<T><<<grid_for(n, L.grid_rows), kBlock, 0, L.stream>>>(n, Ap, Aj, Av, dsq, Ahat);
+    note_launch();
+}
+
+template <class T>
+void launch_qvec_k1(const Launch &L, int n, const int *Pp, const int *Pj, const double *Bc, T *qv) {
+    if (n <= 0) return;
+    k_qvec_k1<T><<<grid_for(n, L.grid_rows), kBlock, 0, L.stream>>>(n, Pp, Pj, Bc, qv);
+    note_launch();
+}
+
+template void launch_scale_a<double>(const Launch &, int, const int *, const int *, const double *,
+                                     const double *, double *);
+template void launch_scale_a<float>(const Launch &, int, const int *, const int *, const double *,
+                                    const double *, float *);
+template void launch_qvec_k1<double>(const Launch &, int, const int *, const int *, const double *,
+                                     double *);
+template void launch_qvec_k1<float>(const Launch &, int, const int *, const int *, const double *,
+                                    float *);
 
 void launch_to_float(const Launch &L, const double *src, float *dst, long long count) {
     if (count <= 0) return;

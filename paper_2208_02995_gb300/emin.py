@@ -263,8 +263,9 @@ def emin_stats(h, cap=4096):
             "n_rank_deficient": nd.value, "n_applied": na.value}
 
 
-def emin_set_timing(h, enable=True):
-    _check(lib().emin_set_timing(h, int(bool(enable))), "emin_set_timing")
+def emin_set_timing(h, period=1):
+    """Time the masked product of every `period`-th iteration (0: off)."""
+    _check(lib().emin_set_timing(h, int(period)), "emin_set_timing")
 
 
 def emin_timing(h):
