@@ -191,6 +191,31 @@ int emin_stats(emin_ctx *ctx, double *dE_hist, int cap, int *n_hist,
 int emin_set_timing(emin_ctx *ctx, int enable);
 int emin_timing(emin_ctx *ctx, double *ms, long long *launches, long long *total_launches);
 
+/*
+ * Allocation-free masked product (the paper has no counterpart; it is a
+ * service for callers that must not let a library allocate device memory,
+ * e.g. processes whose device memory belongs to another allocator's pool or
+ * request paths that cannot afford the device synchronisation of
+ * cudaMalloc / cudaFree).
+ *   out  = mask_P(A Y)   (nnz(P) doubles, P's pattern, CSR order)
+ *   *dot = <Y, out>      (one double)
+ * Every pointer is a device pointer of the current device; A is n x n and P
+ * is n x nc in CSR as for emin_create (sorted columns).  Work is queued on
+ * `stream` (cudaStream_t, NULL = legacy default) and the call returns
+ * without waiting.  No device or host memory is allocated: the reduction
+ * uses a 128 KiB file-scope device array that every GPU loading the library
+ * holds until the process exits.  The first call on a device looks that
+ * array's address up (once per device, with that device current); make
+ * that first call before any stream capture.  Calls share the array, which
+ * keeps the last call's contents (the counters that must start at zero are
+ * cleared on every call), so calls that overlap on the GPU race.
+ * n > 4,194,304 (= 16,384 blocks of 256 rows) returns EMIN_ERR_ARG.  Row
+ * pointers or column indices out of range are skipped and make *dot NaN.
+ */
+int emin_masked_product_noalloc(int n, int nc, const int *A_rowptr, const int *A_col,
+                                const double *A_val, const int *P_rowptr, const int *P_col,
+                                const double *Y, double *out, double *dot, void *stream);
+
 /* Sizes of the context: nnz(A), nnz(P) (either may be NULL). */
 int emin_sizes(emin_ctx *ctx, long long *nnz_a, long long *nnz_p);
 

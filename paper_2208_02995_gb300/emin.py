@@ -36,7 +36,7 @@ EMIN_RANK_PINV = 1
 SYMBOLS = ("emin_default_opts", "emin_create", "emin_set_values", "emin_reset", "emin_iterate",
            "emin_energy", "emin_get_p", "emin_kprod", "emin_outer", "emin_backward",
            "emin_stats", "emin_sizes", "emin_strerror", "emin_destroy", "emin_set_timing",
-           "emin_timing")
+           "emin_timing", "emin_masked_product_noalloc")
 
 
 class emin_opts(ctypes.Structure):
@@ -89,6 +89,8 @@ def lib():
         L.emin_strerror.restype = ctypes.c_char_p
         L.emin_set_timing.argtypes = [_VP, _I]
         L.emin_timing.argtypes = [_VP, _VP, _VP, ctypes.POINTER(ctypes.c_longlong)]
+        L.emin_masked_product_noalloc.argtypes = [_I, _I, _VP, _VP, _VP, _VP, _VP, _VP, _VP,
+                                                  _VP, _VP]
         L.emin_destroy.argtypes = [_VP]
         L.emin_destroy.restype = None
         for s in SYMBOLS:
@@ -276,6 +278,31 @@ def emin_timing(h):
     tot = ctypes.c_longlong(0)
     _check(lib().emin_timing(h, ms.ctypes.data, n.ctypes.data, ctypes.byref(tot)), "emin_timing")
     return {"ms": ms, "launches": n, "total_launches": tot.value}
+
+
+def emin_masked_product_noalloc(n, nc, A_rowptr, A_col, A_val, P_rowptr, P_col, Y, out, dot,
+                                stream=None):
+    """out = mask_P(A Y), dot[0] = <Y, out> for CUDA tensors, without any
+    device allocation by the library (for callers whose device memory is
+    owned by another allocator, or that cannot afford cudaMalloc's device
+    synchronisation).  Queued on `stream` (default: the current torch
+    stream); returns without waiting."""
+    import torch
+    if stream is None:
+        stream = torch.cuda.current_stream().cuda_stream
+    elif hasattr(stream, "cuda_stream"):
+        stream = stream.cuda_stream
+    keep = []
+    args = [_ptr(A_rowptr, np.int32, keep), _ptr(A_col, np.int32, keep),
+            _ptr(A_val, np.float64, keep), _ptr(P_rowptr, np.int32, keep),
+            _ptr(P_col, np.int32, keep), _ptr(Y, np.float64, keep)]
+    for t in (out, dot):
+        if not (_is_cuda_tensor(t) and t.dtype == torch.float64 and t.is_contiguous()):
+            raise ValueError("out and dot must be contiguous float64 CUDA tensors")
+    _check(lib().emin_masked_product_noalloc(int(n), int(nc), *args, out.data_ptr(),
+                                             dot.data_ptr(), stream),
+           "emin_masked_product_noalloc")
+    return out, dot
 
 
 def emin_destroy(h):
