@@ -56,6 +56,8 @@ def parse():
     ap.add_argument("--no-e2e", action="store_true")
     ap.add_argument("--precision", choices=["both", "mixed", "fp64"], default="both",
                     help="profiling aid: run one arm only (the JSON line needs both)")
+    ap.add_argument("--workload", type=int, default=WORKLOAD,
+                    help="profiling aid: another workload (1-5) with --precision mixed|fp64")
     return ap.parse_args()
 
 
@@ -217,14 +219,14 @@ class Clocks:
 # ---------------------------------------------------------------------------
 # our arm
 # ---------------------------------------------------------------------------
-def time_steps(ctx, out, K, W, stream, dist):
+def time_steps(ctx, out, K, W, stream, dist, iters=ITERS):
     """W untimed steps, then K timed steps; CUDA events on the library's
     stream, barrier + synchronize on both sides."""
     import torch
 
     def step():
         ctx.reset()
-        ctx.iterate(ITERS, 0.0)
+        ctx.iterate(iters, 0.0)
         ctx.get_p(out)
 
     for _ in range(W):
@@ -250,7 +252,8 @@ def run_ours(args, dist):
     from paper_2208_02995_gb300.emin import (Context, emin_set_timing, emin_timing)
 
     torch.cuda.set_device(dist.local)
-    prob = inputs.config(WORKLOAD)
+    prob = inputs.config(args.workload)
+    iters = prob.iters
     peaks = {}
     try:
         with open(os.path.join(ROOT, "MEASURED_PEAKS.json")) as f:
@@ -260,7 +263,7 @@ def run_ours(args, dist):
     hbm_peak = float(peaks.get("hbm_gbs", 6800.0))
     hbm_src = "measured" if "hbm_gbs" in peaks else "fallback"
 
-    cand, hits = in_pattern_products(prob)
+    cand, hits = in_pattern_products(prob) if int(np.diff(prob.P_rowptr).max()) <= 8 else (0, 0)
     stream = torch.cuda.Stream()
     results = {}
     precs = ("mixed", "fp64") if args.precision == "both" else (args.precision,)
@@ -274,7 +277,7 @@ def run_ours(args, dist):
         emin_set_timing(ctx.h, 4)
         if clocks:
             clocks.start()
-        ms = time_steps(ctx, out, args.steps, args.warmup, stream, dist)
+        ms = time_steps(ctx, out, args.steps, args.warmup, stream, dist, iters)
         clk = clocks.stop() if clocks else None
         tm = emin_timing(ctx.h)
         emin_set_timing(ctx.h, 0)
@@ -290,9 +293,10 @@ def run_ours(args, dist):
             "P": out.cpu().numpy(),
         }
         ctx.close()
-    if args.precision != "both":
-        r = results[args.precision]
-        return {"precision": args.precision, "ms_per_step": r["ms"] / args.steps,
+    if args.precision != "both" or args.workload != WORKLOAD:
+        r = results[precs[0]]
+        return {"workload": prob.name, "precision": precs[0], "iters": iters,
+                "ms_per_step": r["ms"] / args.steps,
                 "kprod_avg_us": r["kprod_avg_us"], "kernel_ms": r["kernel_share"],
                 "gpu_launches": r["gpu_launches"]}
     # end-to-end through the C ABI from pinned host buffers

@@ -43,6 +43,10 @@ struct emin_ctx {
     float *sa32 = nullptr;
     double *sa64 = nullptr;
     long long nnz_sell = 0;
+    // node-block plan (3 dofs per node, k = 6)
+    int *boff = nullptr;
+    unsigned short *blen = nullptr;
+    unsigned int *bmap = nullptr;
     double *Pstar = nullptr, *t64c = nullptr;
     // restricted PCG workspaces
     Work<double> w64;   // forward, EMIN_FP64
@@ -135,18 +139,21 @@ int sync(emin_ctx *c) { return cuda_status(cudaStreamSynchronize(c->stream)); }
 // masked products on the unscaled A (energy, adjoint right-hand sides)
 Ops<double> plain_ops64(const emin_ctx *c) {
     return Ops<double>{c->n, c->nc, c->k, c->Ap, c->Aj, c->Av, c->Pp, c->Pj, c->Bc, c->Ginv,
-                       nullptr, nullptr, nullptr, nullptr, nullptr, c->maxrow_p, c->lanes};
+                       nullptr, nullptr, nullptr, nullptr, nullptr, c->boff, c->blen, c->bmap,
+                       c->maxrow_p, c->lanes};
 }
 
 // the iteration's operator A^ with its plan
 Ops<double> iter_ops64(const emin_ctx *c) {
     return Ops<double>{c->n, c->nc, c->k, c->Ap, c->Aj, c->Ah64, c->Pp, c->Pj, c->Bc, c->Ginv,
-                       c->qv64, c->sell_ptr, c->sa64, c->soff, c->smap, c->maxrow_p, c->lanes};
+                       c->qv64, c->sell_ptr, c->sa64, c->soff, c->smap, c->boff, c->blen, c->bmap,
+                       c->maxrow_p, c->lanes};
 }
 
 Ops<float> iter_ops32(const emin_ctx *c) {
     return Ops<float>{c->n, c->nc, c->k, c->Ap, c->Aj, c->Ah32, c->Pp, c->Pj, c->Bc32, c->Ginv32,
-                      c->qv32, c->sell_ptr, c->sa32, c->soff, c->smap, c->maxrow_p, c->lanes};
+                      c->qv32, c->sell_ptr, c->sa32, c->soff, c->smap, c->boff, c->blen, c->bmap,
+                      c->maxrow_p, c->lanes};
 }
 
 template <class T>
@@ -404,6 +411,23 @@ int create_impl(emin_ctx *c, const int *A_rowptr, const int *A_col, const double
         if (c->opts.precision == EMIN_MIXED) EMIN_TRY(dalloc(c, &c->sa32, acc));
         else EMIN_TRY(dalloc(c, &c->sa64, acc));
         EMIN_TRY(sync(c));  // the host copy of the offsets must outlive the transfer
+    }
+
+    if (!c->fast_k1) {
+        // node-blocked problems (elasticity): plan of 3 x 3 / 3 x 6 blocks
+        EMIN_TRY(cuda_status(cudaMemsetAsync(c->dint + 3, 0, sizeof(int), c->stream)));
+        if (launch_detect_blocks(c->L, n, c->k, c->Ap, c->Aj, c->Pp, c->Pj, c->dint + 3)) {
+            EMIN_TRY(cuda_status(cudaMemcpyAsync(c->hint + 3, c->dint + 3, sizeof(int),
+                                                 cudaMemcpyDeviceToHost, c->stream)));
+            EMIN_TRY(sync(c));
+            if (c->hint[3] == 0) {
+                const long long ne = block_plan_entries(c->nnz_a);
+                EMIN_TRY(dalloc(c, &c->boff, ne));
+                EMIN_TRY(dalloc(c, &c->blen, ne));
+                EMIN_TRY(dalloc(c, &c->bmap, ne));
+                launch_block_plan(c->L, n, c->Ap, c->Aj, c->Pp, c->Pj, c->boff, c->blen, c->bmap);
+            }
+        }
     }
 
     EMIN_TRY(run_setup(c));

@@ -94,6 +94,11 @@ struct Ops {
     const T *sa;
     const int *soff;
     const unsigned short *smap;
+    // node-block plan (3 dofs per node, k = 6): per stored 3 x 3 block (v,b)
+    // the offset and row length of node b's rows of P and the slot map
+    const int *boff;
+    const unsigned short *blen;
+    const unsigned int *bmap;
     int maxrow;                   // longest row of P
     int lanes;                    // lanes per row of the row kernels (1 or 32)
 };
@@ -181,6 +186,18 @@ void set_iter_attributes();
 int staged_blocks_per_sm();
 void set_adjoint_attributes();
 void launch_state_begin(const Launch &L, DevState *st, double tau);
+
+// ---- node-block kernels (block_kernels.cu) ----
+// returns 1 if it launched the structure test (flag in *bad), 0 if the
+// problem cannot be node-blocked (k != 6 or n not a multiple of 3)
+int launch_detect_blocks(const Launch &L, int n, int k, const int *Ap, const int *Aj,
+                         const int *Pp, const int *Pj, int *bad);
+void launch_block_plan(const Launch &L, int n, const int *Ap, const int *Aj, const int *Pp,
+                       const int *Pj, int *boff, unsigned short *blen, unsigned int *bmap);
+long long block_plan_entries(long long nnz_a);
+template <class T>
+void launch_kprod_blk(const Launch &L, const Ops<T> &o, const T *Y, T *out, int project,
+                      int dot_mode, Work<T> &w, int check_stop);
 
 // ---- adjoint kernels (adjoint_kernels.cu) ----
 void launch_outer(const Launch &L, int n, const int *Ap, const int *Aj, const int *Pp,

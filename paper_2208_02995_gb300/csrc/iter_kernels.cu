@@ -651,6 +651,10 @@ template <class T>
 void launch_kprod(const Launch &L, const Ops<T> &o, const T *Y, T *out, int project, int dot_mode,
                   Work<T> &w, int check_stop) {
     if (o.n <= 0) return;
+    if (o.boff && o.blen && o.bmap) {
+        launch_kprod_blk<T>(L, o, Y, out, project, dot_mode, w, check_stop);
+        return;
+    }
     if (o.k == 1 && o.sell_ptr && o.sa && o.qv && o.maxrow <= 4) {
         if constexpr (sizeof(T) == 4) {
             // one block per group of 8 slices, at most the resident grid
