@@ -136,10 +136,10 @@ int emin_iterate(emin_ctx *ctx, int n_iters, double tol, int *iters_done,
 int emin_energy(emin_ctx *ctx, double *E);
 
 /*
- * Current prolongation P = P0 + dW on P's pattern (nnz(P) doubles).  In
- * EMIN_MIXED the float correction is promoted to double and every row is
- * projected back onto its constraint in double (least-norm correction as in
- * Algorithm 2).
+ * Current prolongation P = P0 + dW on P's pattern (nnz(P) doubles).  The
+ * correction (float in EMIN_MIXED) is promoted to double and every row is
+ * then projected back onto its constraint in double (least-norm correction
+ * as in Algorithm 2); in EMIN_FP64 this changes P at rounding level only.
  */
 int emin_get_p(emin_ctx *ctx, double *P_val_out, int out_on_device);
 

@@ -270,7 +270,9 @@ int read_state(emin_ctx *c, const DevState *st) {
 }
 
 // current P = P0 + D^{-1/2} dW~ on P's pattern, in double, into dst (device);
-// in mixed precision every row is then corrected onto its constraint in double
+// every row is then corrected onto its constraint in double (in FP64 the
+// correction is at rounding level: it removes the drift that the
+// per-iteration projections accumulate when G_i is ill-conditioned)
 int form_p(emin_ctx *c, double *dst) {
     if (c->fast_k1) {
         if (c->opts.precision == EMIN_MIXED)
@@ -278,7 +280,7 @@ int form_p(emin_ctx *c, double *dst) {
                                    c->dsq, c->B, 1, dst);
         else
             launch_final_k1<double>(c->L, c->n, c->Pp, c->Pj, c->Bc, c->Ginv, c->P0, c->w64.X,
-                                    c->dsq, c->B, 0, dst);
+                                    c->dsq, c->B, 1, dst);
         return check_launch();
     }
     if (c->opts.precision == EMIN_MIXED)
@@ -286,7 +288,7 @@ int form_p(emin_ctx *c, double *dst) {
                        c->w32.X, c->dsq, 1, dst);
     else
         launch_restore(c->L, c->n, c->k, c->Pp, c->Pj, c->Bc, c->B, c->Ginv, c->P0, c->w64.X,
-                       nullptr, c->dsq, 0, dst);
+                       nullptr, c->dsq, 1, dst);
     return check_launch();
 }
 
