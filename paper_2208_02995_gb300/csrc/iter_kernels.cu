@@ -285,7 +285,9 @@ k_kprod_k1_sell(int n, const int *__restrict__ sell_ptr, const T *__restrict__ s
         }
     }
     for (; sl < nslices; sl += nwarps) {
-        const int base = nb0, len = (nb1 - nb0) >> 5, p0 = np0, m = np1 - np0;
+        // lanes past the last row (ragged last slice) take no entries
+        const int base = nb0, len = (sl * 32 + lane < n) ? (nb1 - nb0) >> 5 : 0;
+        const int p0 = np0, m = np1 - np0;
         const T *pa = sa + base + lane;
         const int *po = soff + base + lane;
         const unsigned short *pm = smap + base + lane;
@@ -439,7 +441,7 @@ k_kprod_k1_staged(int n, const int *__restrict__ sell_ptr, const float *__restri
         __syncthreads();
         if (have) {
             const int gb = sPtr[b][warp];
-            const int len = (sPtr[b][warp + 1] - gb) >> 5;
+            const int len = valid ? (sPtr[b][warp + 1] - gb) >> 5 : 0;
             const int lb = gb - sPtr[b][0];
             const bool fit = sFit[b] != 0;
             float a0 = 0.f, a1 = 0.f, a2 = 0.f, a3 = 0.f;

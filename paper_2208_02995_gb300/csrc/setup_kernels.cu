@@ -405,22 +405,27 @@ __global__ void k_sell_len(int n, const int *__restrict__ Ap, int *slen) {
 // once) in SELL-32 order: for every stored (i, l) of A, the offset of row l
 // of P and, for each slot s < 4 of row i, the position q of the same column
 // in row l (3 bits, 7 if absent).  Padding entries carry no slot (map 0xFFF)
-// and offset 0.  Requires rows of P with at most 4 entries.
+// and offset 0; that includes every entry of the lanes past row n - 1 in a
+// ragged last slice, so that no entry of the plan is left unwritten.
+// Requires rows of P with at most 4 entries.
 __global__ void k_sell_plan(int n, const int *__restrict__ Ap, const int *__restrict__ Aj,
                             const int *__restrict__ Pp, const int *__restrict__ Pj,
                             const int *__restrict__ sell_ptr, int *soff, unsigned short *smap,
                             int *dpos) {
-    for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < n; i += gridDim.x * blockDim.x) {
+    const int nlanes = ((n + 31) >> 5) << 5;
+    for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < nlanes; i += gridDim.x * blockDim.x) {
         const int sl = i >> 5, lane = i & 31;
         const int base = sell_ptr[sl], len = (sell_ptr[sl + 1] - base) >> 5;
-        const int p0 = Pp[i], m = Pp[i + 1] - p0, e0 = Ap[i], rl = Ap[i + 1] - e0;
+        const bool row = i < n;
+        const int p0 = row ? Pp[i] : 0, m = row ? Pp[i + 1] - p0 : 0;
+        const int e0 = row ? Ap[i] : 0, rl = row ? Ap[i + 1] - e0 : 0;
         int J[4];
 #pragma unroll
         for (int s = 0; s < 4; ++s) J[s] = (s < m) ? Pj[p0 + s] : -1;
         int dp = -1;
         for (int j = 0; j < rl; ++j)
             if (Aj[e0 + j] == i) dp = e0 + j;
-        dpos[i] = dp;  // position of A(i,i) in the CSR arrays (-1: missing)
+        if (row) dpos[i] = dp;  // position of A(i,i) in the CSR arrays (-1: missing)
         for (int j = 0; j < len; ++j) {
             const int pos = base + j * 32 + lane;
             unsigned int map = 0xFFFu;
