@@ -222,6 +222,11 @@ int emin_sizes(emin_ctx *ctx, long long *nnz_a, long long *nnz_p);
 /* Static description of a status code. */
 const char *emin_strerror(int status);
 
+/* The last CUDA failure seen by a library call of this thread (the failing
+ * step and CUDA's error name and text), "" if none; valid until the next
+ * call of this thread. */
+const char *emin_last_error(void);
+
 /* Release every resource of the context (NULL is accepted). */
 void emin_destroy(emin_ctx *ctx);
 

@@ -47,6 +47,8 @@ struct emin_ctx {
     int *boff = nullptr;
     unsigned short *blen = nullptr;
     unsigned int *bmap = nullptr;
+    int *tile_map = nullptr;
+    int ntiles = 0;
     double *Pstar = nullptr, *t64c = nullptr;
     // restricted PCG workspaces
     Work<double> w64;   // forward, EMIN_FP64
@@ -78,6 +80,8 @@ long long launches_so_far() { return g_launches.load(std::memory_order_relaxed);
 
 namespace {
 
+thread_local char g_last_error[256] = "";
+
 struct DeviceGuard {
     int prev = -1;
     explicit DeviceGuard(int dev) {
@@ -95,7 +99,10 @@ int dalloc(emin_ctx *c, T **p, long long count) {
     size_t bytes = (size_t)(count > 0 ? count : 1) * sizeof(T);
     bytes = (bytes + 255) & ~(size_t)255;
     void *q = nullptr;
-    if (cudaMalloc(&q, bytes) != cudaSuccess) {
+    const cudaError_t e = cudaMalloc(&q, bytes);
+    if (e != cudaSuccess) {
+        std::snprintf(g_last_error, sizeof(g_last_error), "cudaMalloc(%zu): %s", bytes,
+                      cudaGetErrorName(e));
         cudaGetLastError();
         return EMIN_ERR_NOMEM;
     }
@@ -104,13 +111,18 @@ int dalloc(emin_ctx *c, T **p, long long count) {
     return EMIN_OK;
 }
 
-int cuda_status(cudaError_t e) {
+int cuda_status_at(cudaError_t e, const char *where) {
     if (e == cudaSuccess) return EMIN_OK;
+    std::snprintf(g_last_error, sizeof(g_last_error), "%s: %s (%s)", where, cudaGetErrorName(e),
+                  cudaGetErrorString(e));
     cudaGetLastError();
     return e == cudaErrorMemoryAllocation ? EMIN_ERR_NOMEM : EMIN_ERR_CUDA;
 }
 
-int check_launch() { return cuda_status(cudaGetLastError()); }
+#define cuda_status(e) cuda_status_at((e), __func__)
+
+int check_launch_at(const char *where) { return cuda_status_at(cudaGetLastError(), where); }
+#define check_launch() check_launch_at(__func__)
 
 #define EMIN_TRY(expr)                   \
     do {                                 \
@@ -139,20 +151,20 @@ int sync(emin_ctx *c) { return cuda_status(cudaStreamSynchronize(c->stream)); }
 // masked products on the unscaled A (energy, adjoint right-hand sides)
 Ops<double> plain_ops64(const emin_ctx *c) {
     return Ops<double>{c->n, c->nc, c->k, c->Ap, c->Aj, c->Av, c->Pp, c->Pj, c->Bc, c->Ginv,
-                       nullptr, nullptr, nullptr, nullptr, nullptr, c->boff, c->blen, c->bmap,
+                       nullptr, nullptr, nullptr, nullptr, nullptr, c->boff, c->blen, c->bmap, c->tile_map, c->ntiles,
                        c->maxrow_p, c->lanes};
 }
 
 // the iteration's operator A^ with its plan
 Ops<double> iter_ops64(const emin_ctx *c) {
     return Ops<double>{c->n, c->nc, c->k, c->Ap, c->Aj, c->Ah64, c->Pp, c->Pj, c->Bc, c->Ginv,
-                       c->qv64, c->sell_ptr, c->sa64, c->soff, c->smap, c->boff, c->blen, c->bmap,
+                       c->qv64, c->sell_ptr, c->sa64, c->soff, c->smap, c->boff, c->blen, c->bmap, c->tile_map, c->ntiles,
                        c->maxrow_p, c->lanes};
 }
 
 Ops<float> iter_ops32(const emin_ctx *c) {
     return Ops<float>{c->n, c->nc, c->k, c->Ap, c->Aj, c->Ah32, c->Pp, c->Pj, c->Bc32, c->Ginv32,
-                      c->qv32, c->sell_ptr, c->sa32, c->soff, c->smap, c->boff, c->blen, c->bmap,
+                      c->qv32, c->sell_ptr, c->sa32, c->soff, c->smap, c->boff, c->blen, c->bmap, c->tile_map, c->ntiles,
                       c->maxrow_p, c->lanes};
 }
 
@@ -428,6 +440,35 @@ int create_impl(emin_ctx *c, const int *A_rowptr, const int *A_col, const double
                 EMIN_TRY(dalloc(c, &c->blen, ne));
                 EMIN_TRY(dalloc(c, &c->bmap, ne));
                 launch_block_plan(c->L, n, c->Ap, c->Aj, c->Pp, c->Pj, c->boff, c->blen, c->bmap);
+                // warp tiles of output blocks: whole nodes per warp, packed greedily
+                const int nn = n / 3;
+                int *dna = nullptr;
+                EMIN_TRY(dalloc(c, &dna, nn));
+                launch_node_slots(c->L, n, c->Pp, dna);
+                std::vector<int> na(nn);
+                EMIN_TRY(cuda_status(cudaMemcpyAsync(na.data(), dna, sizeof(int) * nn,
+                                                     cudaMemcpyDeviceToHost, c->stream)));
+                EMIN_TRY(sync(c));
+                std::vector<int> tm;
+                tm.reserve((size_t)nn * 6);
+                int fill = 0;
+                for (int v = 0; v < nn; ++v) {
+                    if (fill + na[v] > 32) {
+                        while (fill < 32) { tm.push_back(-1); ++fill; }
+                        fill = 0;
+                    }
+                    for (int s2 = 0; s2 < na[v]; ++s2) tm.push_back((v << 3) | s2);
+                    fill += na[v];
+                }
+                while (fill % 32) { tm.push_back(-1); ++fill; }
+                c->ntiles = (int)(tm.size() / 32);
+                if (c->ntiles > 0) {
+                    EMIN_TRY(dalloc(c, &c->tile_map, (long long)tm.size()));
+                    EMIN_TRY(cuda_status(cudaMemcpyAsync(c->tile_map, tm.data(),
+                                                         sizeof(int) * tm.size(),
+                                                         cudaMemcpyHostToDevice, c->stream)));
+                    EMIN_TRY(sync(c));
+                }
             }
         }
     }
@@ -530,6 +571,8 @@ void emin_default_opts(emin_opts *opts) {
     opts->checks = 0;
     opts->stream = nullptr;
 }
+
+const char *emin_last_error(void) { return g_last_error; }
 
 const char *emin_strerror(int status) {
     switch (status) {

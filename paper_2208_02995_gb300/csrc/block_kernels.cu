@@ -258,6 +258,188 @@ k_kprod_blk(int nn, const int *__restrict__ Ap, const T *__restrict__ Av,
     }
 }
 
+// ---------------------------------------------------------------------------
+// Output-block kernel: one lane per output block (node v, aggregate slot s)
+// = the 3 x 6 block of P rows 3v..3v+2, columns 6 g_s .. 6 g_s + 5.  Warps
+// hold whole nodes (a tile map, built once, lists the blocks of each warp
+// with -1 padding), so the per-row projection reduces over the lanes of one
+// node through shared memory.  Per neighbour b holding g_s the lane loads
+// the 3 x 3 block A^_vb (lanes of one node load the same addresses) and the
+// 3 x 6 block Y_(b, g_s) as 8-byte pairs (rows of P have multiples of 6
+// entries, so every block column pair is 8-byte aligned), then does the 54
+// products of A_vb Y_(b, g_s).
+// ---------------------------------------------------------------------------
+template <class T>
+struct Pair;
+template <>
+struct Pair<float> {
+    using V = float2;
+};
+template <>
+struct Pair<double> {
+    using V = double2;
+};
+
+template <class T>
+__global__ void __launch_bounds__(kBlock)
+k_kprod_blk2(int ntiles, const int *__restrict__ tile_map, const int *__restrict__ Ap,
+             const T *__restrict__ Av, const int *__restrict__ Pp, const int *__restrict__ Pj,
+             const int *__restrict__ boff, const unsigned short *__restrict__ blen,
+             const unsigned int *__restrict__ bmap, const T *__restrict__ Bc,
+             const T *__restrict__ Ginv, const T *__restrict__ Y, T *__restrict__ out,
+             int project, int dot_mode, DevState *st, double *partials, double *hist, int cap,
+             int check_stop) {
+    if (check_stop && st->stop) return;
+    using V = typename Pair<T>::V;
+    constexpr int KK = KB * (KB + 1) / 2;
+    constexpr int NW = kBlock / 32;
+    constexpr int R = NB * KB;  // 18 partial sums per lane: t_r[a]
+    __shared__ T sT[NW][32][R + 1];
+    const int w = threadIdx.x >> 5, lane = threadIdx.x & 31;
+    Dot<T> dot;
+    for (int tile = (blockIdx.x * blockDim.x + threadIdx.x) >> 5; tile < ntiles;
+         tile += (gridDim.x * blockDim.x) >> 5) {
+        const int code = tile_map[tile * 32 + lane];
+        const bool valid = code >= 0;
+        const int v = valid ? code >> 3 : 0, s = code & 7;
+        int a0 = 0, deg = 0, p0 = 0, mrow = 0, c0 = 0;
+        if (valid) {
+            a0 = Ap[NB * v];
+            deg = (Ap[NB * v + 1] - a0) / NB;
+            p0 = Pp[NB * v];
+            mrow = Pp[NB * v + 1] - p0;
+            c0 = Pj[p0 + KB * s];
+        }
+        const int ne0 = a0 / (NB * NB), rs = NB * deg;
+        T acc[NB][KB];
+#pragma unroll
+        for (int r = 0; r < NB; ++r)
+#pragma unroll
+            for (int t = 0; t < KB; ++t) acc[r][t] = T(0);
+#pragma unroll 2
+        for (int j = 0; j < deg; ++j) {
+            const unsigned int q = (bmap[ne0 + j] >> (4 * s)) & 0xFu;
+            if (q < (unsigned)kMaxSlots) {
+                const int yb = boff[ne0 + j] + KB * (int)q, yl = blen[ne0 + j];
+                T a[NB][NB];
+#pragma unroll
+                for (int r = 0; r < NB; ++r)
+#pragma unroll
+                    for (int c = 0; c < NB; ++c) a[r][c] = Av[a0 + r * rs + NB * j + c];
+                T y[NB][KB];
+#pragma unroll
+                for (int c = 0; c < NB; ++c) {
+                    const V *yp = reinterpret_cast<const V *>(Y + yb + c * yl);
+#pragma unroll
+                    for (int h = 0; h < KB / 2; ++h) {
+                        const V u = yp[h];
+                        y[c][2 * h] = u.x;
+                        y[c][2 * h + 1] = u.y;
+                    }
+                }
+#pragma unroll
+                for (int r = 0; r < NB; ++r)
+#pragma unroll
+                    for (int t = 0; t < KB; ++t)
+                        acc[r][t] = fmat(a[r][0], y[0][t],
+                                         fmat(a[r][1], y[1][t], fmat(a[r][2], y[2][t], acc[r][t])));
+            }
+        }
+        if (project) {
+            // B_i restricted to this block's columns: the rows c0..c0+5 of B_c
+            T bc[KB][KB];
+#pragma unroll
+            for (int t = 0; t < KB; ++t)
+#pragma unroll
+                for (int a = 0; a < KB; ++a) bc[t][a] = valid ? Bc[(size_t)(c0 + t) * KB + a] : T(0);
+            // this block's share of t_r = B_i^T x_r, then the sum over the node's lanes
+#pragma unroll
+            for (int r = 0; r < NB; ++r)
+#pragma unroll
+                for (int a = 0; a < KB; ++a) {
+                    T v2 = T(0);
+#pragma unroll
+                    for (int t = 0; t < KB; ++t) v2 = fmat(bc[t][a], acc[r][t], v2);
+                    sT[w][lane][r * KB + a] = v2;
+                }
+            __syncwarp();
+            // the node's lanes are consecutive: first lane = lane - s
+            const int first = lane - s;
+            T tv[NB][KB];
+#pragma unroll
+            for (int r = 0; r < NB; ++r)
+#pragma unroll
+                for (int a = 0; a < KB; ++a) tv[r][a] = T(0);
+            if (valid) {
+                const int nslot = mrow / KB;
+                for (int u = 0; u < nslot; ++u)
+#pragma unroll
+                    for (int r = 0; r < NB; ++r)
+#pragma unroll
+                        for (int a = 0; a < KB; ++a) tv[r][a] += sT[w][first + u][r * KB + a];
+            }
+            __syncwarp();
+            // c_r = G^{-1} t_r (the node's three rows share J_i, hence G_i)
+            T g[KK];
+#pragma unroll
+            for (int e = 0; e < KK; ++e) g[e] = valid ? Ginv[(size_t)NB * v * KK + e] : T(0);
+#pragma unroll
+            for (int r = 0; r < NB; ++r) {
+                T cv[KB];
+#pragma unroll
+                for (int a = 0; a < KB; ++a) {
+                    T v2 = T(0);
+#pragma unroll
+                    for (int c = 0; c < KB; ++c) v2 = fmat(g[a >= c ? tri(a, c) : tri(c, a)], tv[r][c], v2);
+                    cv[a] = v2;
+                }
+#pragma unroll
+                for (int t = 0; t < KB; ++t) {
+                    T x = acc[r][t];
+#pragma unroll
+                    for (int a = 0; a < KB; ++a) x = fmat(-bc[t][a], cv[a], x);
+                    acc[r][t] = x;
+                }
+            }
+        }
+        if (valid) {
+#pragma unroll
+            for (int r = 0; r < NB; ++r) {
+                const int o = p0 + r * mrow + KB * s;
+                V *op = reinterpret_cast<V *>(out + o);
+                const V *yo = reinterpret_cast<const V *>(Y + o);
+#pragma unroll
+                for (int h = 0; h < KB / 2; ++h) {
+                    V u;
+                    u.x = acc[r][2 * h];
+                    u.y = acc[r][2 * h + 1];
+                    op[h] = u;
+                    if (dot_mode) {
+                        const V yv = yo[h];
+                        dot.add(yv.x, u.x);
+                        dot.add(yv.y, u.y);
+                    }
+                }
+            }
+        }
+    }
+    if (dot_mode) {
+        __shared__ double sh[32];
+        double bt = block_dot_total(dot, sh);
+        double total;
+        if (grid_reduce(bt, partials, &st->ticket[0], &total)) {
+            if (dot_mode == DOT_ALPHA) finalize_alpha(st, total, hist, cap);
+            else st->aux = total;
+        }
+    }
+}
+
+// aggregate slots per node (for the host-side tile packing)
+__global__ void k_node_slots(int nn, const int *__restrict__ Pp, int *na) {
+    for (int v = blockIdx.x * blockDim.x + threadIdx.x; v < nn; v += gridDim.x * blockDim.x)
+        na[v] = (Pp[NB * v + 1] - Pp[NB * v]) / KB;
+}
+
 }  // namespace
 
 int launch_detect_blocks(const Launch &L, int n, int k, const int *Ap, const int *Aj,
@@ -278,11 +460,27 @@ void launch_block_plan(const Launch &L, int n, const int *Ap, const int *Aj, con
     note_launch();
 }
 
+void launch_node_slots(const Launch &L, int n, const int *Pp, int *na) {
+    const int nn = n / NB;
+    if (nn <= 0) return;
+    k_node_slots<<<grid_for(nn, L.grid_rows), kBlock, 0, L.stream>>>(nn, Pp, na);
+    note_launch();
+}
+
 template <class T>
 void launch_kprod_blk(const Launch &L, const Ops<T> &o, const T *Y, T *out, int project,
                       int dot_mode, Work<T> &w, int check_stop) {
     const int nn = o.n / NB;
     if (nn <= 0) return;
+    if (o.tile_map && o.ntiles > 0) {
+        const int g = grid_for((long long)o.ntiles * 32, L.grid_warps);
+        k_kprod_blk2<T><<<g, kBlock, 0, L.stream>>>(o.ntiles, o.tile_map, o.Ap, o.Av, o.Pp, o.Pj,
+                                                     o.boff, o.blen, o.bmap, o.Bc, o.Ginv, Y, out,
+                                                     project, dot_mode, w.st, w.partials, w.hist,
+                                                     w.hist_cap, check_stop);
+        note_launch();
+        return;
+    }
     const int g = grid_for((long long)nn * 32, L.grid_warps);
     k_kprod_blk<T><<<g, kBlock, 0, L.stream>>>(nn, o.Ap, o.Av, o.Pp, o.Pj, o.boff, o.blen, o.bmap,
                                                 o.Bc, o.Ginv, Y, out, project, dot_mode, w.st,

@@ -99,6 +99,9 @@ struct Ops {
     const int *boff;
     const unsigned short *blen;
     const unsigned int *bmap;
+    // warp tiles of output blocks (node v, slot s) coded v << 3 | s, -1 padding
+    const int *tile_map;
+    int ntiles;
     int maxrow;                   // longest row of P
     int lanes;                    // lanes per row of the row kernels (1 or 32)
 };
@@ -195,6 +198,7 @@ int launch_detect_blocks(const Launch &L, int n, int k, const int *Ap, const int
 void launch_block_plan(const Launch &L, int n, const int *Ap, const int *Aj, const int *Pp,
                        const int *Pj, int *boff, unsigned short *blen, unsigned int *bmap);
 long long block_plan_entries(long long nnz_a);
+void launch_node_slots(const Launch &L, int n, const int *Pp, int *na);
 template <class T>
 void launch_kprod_blk(const Launch &L, const Ops<T> &o, const T *Y, T *out, int project,
                       int dot_mode, Work<T> &w, int check_stop);

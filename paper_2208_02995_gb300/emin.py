@@ -36,7 +36,7 @@ EMIN_RANK_PINV = 1
 SYMBOLS = ("emin_default_opts", "emin_create", "emin_set_values", "emin_reset", "emin_iterate",
            "emin_energy", "emin_get_p", "emin_kprod", "emin_outer", "emin_backward",
            "emin_stats", "emin_sizes", "emin_strerror", "emin_destroy", "emin_set_timing",
-           "emin_timing", "emin_masked_product_noalloc")
+           "emin_timing", "emin_masked_product_noalloc", "emin_last_error")
 
 
 class emin_opts(ctypes.Structure):
@@ -48,7 +48,9 @@ class emin_opts(ctypes.Structure):
 class EminError(RuntimeError):
     def __init__(self, status, call):
         self.status = status
-        super().__init__(f"{call}: {strerror(status)} (status {status})")
+        detail = emin_last_error() if status in (EMIN_ERR_CUDA, EMIN_ERR_NOMEM) else ""
+        super().__init__(f"{call}: {strerror(status)} (status {status})"
+                         + (f" [{detail}]" if detail else ""))
 
 
 _lib = None
@@ -87,6 +89,8 @@ def lib():
                                  ctypes.POINTER(ctypes.c_longlong)]
         L.emin_strerror.argtypes = [_I]
         L.emin_strerror.restype = ctypes.c_char_p
+        L.emin_last_error.argtypes = []
+        L.emin_last_error.restype = ctypes.c_char_p
         L.emin_set_timing.argtypes = [_VP, _I]
         L.emin_timing.argtypes = [_VP, _VP, _VP, ctypes.POINTER(ctypes.c_longlong)]
         L.emin_masked_product_noalloc.argtypes = [_I, _I, _VP, _VP, _VP, _VP, _VP, _VP, _VP,
@@ -94,7 +98,7 @@ def lib():
         L.emin_destroy.argtypes = [_VP]
         L.emin_destroy.restype = None
         for s in SYMBOLS:
-            if s not in ("emin_default_opts", "emin_strerror", "emin_destroy"):
+            if s not in ("emin_default_opts", "emin_strerror", "emin_destroy", "emin_last_error"):
                 getattr(L, s).restype = _I
         _lib = L
     return _lib
@@ -106,6 +110,10 @@ def strerror(status: int) -> str:
 
 def emin_strerror(status: int) -> str:
     return strerror(status)
+
+
+def emin_last_error() -> str:
+    return lib().emin_last_error().decode()
 
 
 def _check(status, call):
