@@ -339,7 +339,7 @@ def run_ours(args, dist):
             "in_pattern_products": hits,
         },
         "roofline": {
-            "kernel": "masked product + projection + y^T y_ (k_kprod_k1_staged, float)",
+            "kernel": "masked product + projection + y^T y_ (k_kprod_k1_pk<float>, packed SELL-32 plan)",
             "bound": "hbm",
             "achieved": ach,
             "peak": hbm_peak,

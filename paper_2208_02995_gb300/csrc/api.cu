@@ -40,6 +40,8 @@ struct emin_ctx {
     // k = 1 plan of the fixed pattern (built once per context), SELL-32 order
     int *sell_ptr = nullptr, *soff = nullptr, *dpos = nullptr;
     unsigned short *smap = nullptr;
+    unsigned int *sw = nullptr;  // packed words (null: some offset difference is too wide)
+    uint2 *spk32 = nullptr;      // float values interleaved with the packed words
     float *sa32 = nullptr;
     double *sa64 = nullptr;
     long long nnz_sell = 0;
@@ -111,6 +113,19 @@ int dalloc(emin_ctx *c, T **p, long long count) {
     return EMIN_OK;
 }
 
+// releases one allocation made by dalloc before the context is destroyed
+template <class T>
+void dfree(emin_ctx *c, T *&p) {
+    if (!p) return;
+    for (size_t i = 0; i < c->dev_allocs.size(); ++i)
+        if (c->dev_allocs[i] == static_cast<void *>(p)) {
+            cudaFree(c->dev_allocs[i]);
+            c->dev_allocs.erase(c->dev_allocs.begin() + (long)i);
+            break;
+        }
+    p = nullptr;
+}
+
 int cuda_status_at(cudaError_t e, const char *where) {
     if (e == cudaSuccess) return EMIN_OK;
     std::snprintf(g_last_error, sizeof(g_last_error), "%s: %s (%s)", where, cudaGetErrorName(e),
@@ -151,20 +166,20 @@ int sync(emin_ctx *c) { return cuda_status(cudaStreamSynchronize(c->stream)); }
 // masked products on the unscaled A (energy, adjoint right-hand sides)
 Ops<double> plain_ops64(const emin_ctx *c) {
     return Ops<double>{c->n, c->nc, c->k, c->Ap, c->Aj, c->Av, c->Pp, c->Pj, c->Bc, c->Ginv,
-                       nullptr, nullptr, nullptr, nullptr, nullptr, c->boff, c->blen, c->bmap, c->tile_map, c->ntiles,
+                       nullptr, nullptr, nullptr, nullptr, nullptr, nullptr, nullptr, c->boff, c->blen, c->bmap, c->tile_map, c->ntiles,
                        c->maxrow_p, c->lanes};
 }
 
 // the iteration's operator A^ with its plan
 Ops<double> iter_ops64(const emin_ctx *c) {
     return Ops<double>{c->n, c->nc, c->k, c->Ap, c->Aj, c->Ah64, c->Pp, c->Pj, c->Bc, c->Ginv,
-                       c->qv64, c->sell_ptr, c->sa64, c->soff, c->smap, c->boff, c->blen, c->bmap, c->tile_map, c->ntiles,
+                       c->qv64, c->sell_ptr, c->sa64, c->soff, c->smap, c->sw, nullptr, c->boff, c->blen, c->bmap, c->tile_map, c->ntiles,
                        c->maxrow_p, c->lanes};
 }
 
 Ops<float> iter_ops32(const emin_ctx *c) {
     return Ops<float>{c->n, c->nc, c->k, c->Ap, c->Aj, c->Ah32, c->Pp, c->Pj, c->Bc32, c->Ginv32,
-                      c->qv32, c->sell_ptr, c->sa32, c->soff, c->smap, c->boff, c->blen, c->bmap, c->tile_map, c->ntiles,
+                      c->qv32, c->sell_ptr, c->sa32, c->soff, c->smap, c->sw, c->spk32, c->boff, c->blen, c->bmap, c->tile_map, c->ntiles,
                       c->maxrow_p, c->lanes};
 }
 
@@ -224,7 +239,8 @@ int run_setup(emin_ctx *c) {
                                    c->opts.rank_policy, c->dint, c->dint + 2, c->dsq, c->dhalf,
                                    c->Ginv, c->qv32, c->P0, c->t32a);
             launch_to_float(L, c->Bc, c->Bc32, (long long)c->nc * c->k);
-            launch_sell_values<float>(L, c->n, c->Ap, c->Aj, c->Av, c->dsq, c->sell_ptr, c->sa32);
+            launch_sell_values<float>(L, c->n, c->Ap, c->Aj, c->Av, c->dsq, c->sell_ptr, c->sa32,
+                                      c->sw, c->spk32);
             EMIN_TRY(start_pcg<float>(c, iter_ops32(c), c->w32, c->t32a));
         } else {
             launch_setup_k1<double>(L, c->n, c->dpos, c->Av, c->Pp, c->Pj, c->Bc, c->B, c->P0_in,
@@ -247,7 +263,8 @@ int run_setup(emin_ctx *c) {
     if (c->opts.precision == EMIN_MIXED) {
         launch_to_float(L, c->Bc, c->Bc32, (long long)c->nc * c->k);
         if (c->sell_ptr)
-            launch_sell_values<float>(L, c->n, c->Ap, c->Aj, c->Av, c->dsq, c->sell_ptr, c->sa32);
+            launch_sell_values<float>(L, c->n, c->Ap, c->Aj, c->Av, c->dsq, c->sell_ptr, c->sa32,
+                                      c->sw, c->spk32);
         else
             launch_scale_a<float>(L, c->n, c->Ap, c->Aj, c->Av, c->dsq, c->Ah32);
         if (c->k == 1) launch_qvec_k1<float>(L, c->n, c->Pp, c->Pj, c->Bc, c->qv32);
@@ -419,12 +436,27 @@ int create_impl(emin_ctx *c, const int *A_rowptr, const int *A_col, const double
                                              cudaMemcpyHostToDevice, c->stream)));
         EMIN_TRY(dalloc(c, &c->soff, acc));
         EMIN_TRY(dalloc(c, &c->smap, acc));
+        EMIN_TRY(dalloc(c, &c->sw, acc));
         EMIN_TRY(dalloc(c, &c->dpos, n));
+        EMIN_TRY(cuda_status(cudaMemsetAsync(c->dint + 3, 0, sizeof(int), c->stream)));
         launch_sell_plan(c->L, n, c->Ap, c->Aj, c->Pp, c->Pj, c->sell_ptr, c->soff, c->smap,
-                         c->dpos);
-        if (c->opts.precision == EMIN_MIXED) EMIN_TRY(dalloc(c, &c->sa32, acc));
-        else EMIN_TRY(dalloc(c, &c->sa64, acc));
+                         c->sw, c->dint + 3, c->dpos);
+        EMIN_TRY(cuda_status(cudaMemcpyAsync(c->hint + 3, c->dint + 3, sizeof(int),
+                                             cudaMemcpyDeviceToHost, c->stream)));
         EMIN_TRY(sync(c));  // the host copy of the offsets must outlive the transfer
+        // the packed plan when every offset difference fits its word, else the plain one
+        if (c->hint[3] == 0) {
+            dfree(c, c->soff);
+            dfree(c, c->smap);
+        } else {
+            dfree(c, c->sw);
+        }
+        if (c->opts.precision == EMIN_MIXED) {
+            if (c->sw) EMIN_TRY(dalloc(c, &c->spk32, acc));
+            else EMIN_TRY(dalloc(c, &c->sa32, acc));
+        } else {
+            EMIN_TRY(dalloc(c, &c->sa64, acc));
+        }
     }
 
     if (!c->fast_k1) {
@@ -642,6 +674,10 @@ int emin_create(emin_ctx **out, int n, int nc, int k, const int *A_rowptr, const
     if (c->L.grid_rows > kMaxGrid) c->L.grid_rows = kMaxGrid;
     c->L.grid_staged = nsm * staged_blocks_per_sm();
     if (c->L.grid_staged > kMaxGrid) c->L.grid_staged = kMaxGrid;
+    c->L.grid_pk32 = nsm * pk_blocks_per_sm(0);
+    if (c->L.grid_pk32 > kMaxGrid) c->L.grid_pk32 = kMaxGrid;
+    c->L.grid_pk64 = nsm * pk_blocks_per_sm(1);
+    if (c->L.grid_pk64 > kMaxGrid) c->L.grid_pk64 = kMaxGrid;
     if (c->L.grid_warps > kMaxGrid) c->L.grid_warps = kMaxGrid;
     set_iter_attributes();
     set_adjoint_attributes();

@@ -94,6 +94,12 @@ struct Ops {
     const T *sa;
     const int *soff;
     const unsigned short *smap;
+    // packed form of the same plan: per entry one word (o - p0_i) << 12 | map,
+    // o the offset of row l of P and p0_i that of the entry's own row (null
+    // when some offset difference does not fit 20 bits); for float the value
+    // and the word are interleaved (spk), for double they are separate (sa, sw)
+    const unsigned int *sw;
+    const uint2 *spk;
     // node-block plan (3 dofs per node, k = 6): per stored 3 x 3 block (v,b)
     // the offset and row length of node b's rows of P and the slot map
     const int *boff;
@@ -111,6 +117,8 @@ struct Launch {
     int grid_rows;    // grid of thread-per-row kernels
     int grid_warps;   // grid of warp-per-row kernels
     int grid_staged;  // resident grid of the staged masked product
+    int grid_pk32;    // resident grids of the packed-plan masked product (float, double)
+    int grid_pk64;
 };
 
 // shared-memory slots per warp for a row of P: the longest row rounded up
@@ -158,12 +166,17 @@ void launch_final_k1(const Launch &L, int n, const int *Pp, const int *Pj, const
 // SELL-32 plan: slice lengths (longest row of A per 32 rows), then the plan
 // in slice order once sell_ptr (exclusive scan of 32 * length) is known
 void launch_sell_len(const Launch &L, int n, const int *Ap, int *slen);
+// sw may be null (no packed words); *wide is set when an offset difference
+// does not fit the packed word
 void launch_sell_plan(const Launch &L, int n, const int *Ap, const int *Aj, const int *Pp,
                       const int *Pj, const int *sell_ptr, int *soff, unsigned short *smap,
-                      int *dpos);
+                      unsigned int *sw, int *wide, int *dpos);
+// A^ in plan order into sa, or (float, spk non-null) interleaved with the
+// packed words sw into spk
 template <class T>
 void launch_sell_values(const Launch &L, int n, const int *Ap, const int *Aj, const double *Av,
-                        const double *dsq, const int *sell_ptr, T *sa);
+                        const double *dsq, const int *sell_ptr, T *sa,
+                        const unsigned int *sw = nullptr, uint2 *spk = nullptr);
 template <class T>
 void launch_scale_a(const Launch &L, int n, const int *Ap, const int *Aj, const double *Av,
                     const double *dsq, T *Ahat);
@@ -187,6 +200,7 @@ void launch_row_scale(const Launch &L, int n, const int *Pp, int lanes, const do
 void launch_state_reset(const Launch &L, DevState *st);
 void set_iter_attributes();
 int staged_blocks_per_sm();
+int pk_blocks_per_sm(int double_precision);
 void set_adjoint_attributes();
 void launch_state_begin(const Launch &L, DevState *st, double tau);
 

@@ -497,6 +497,139 @@ k_kprod_k1_staged(int n, const int *__restrict__ sell_ptr, const float *__restri
     }
 }
 
+// ---------------------------------------------------------------------------
+// The same product on the packed plan: one 8-byte record per entry for float
+// ({a^_il, word}) or a double value plus a word, read straight from global
+// memory (coalesced, streaming), one warp per slice, one lane per row.  The
+// word gives row l's offset relative to the lane's own row and the slot map,
+// so that one load per entry replaces the three of the plain plan.  A slice's
+// length and the largest row of P among its 32 rows are uniform over the
+// warp; the loop body is specialised for both (exact entry count, only the
+// slots that some row of the slice has), so no instruction is spent on
+// padding steps or on slots no row holds.
+// ---------------------------------------------------------------------------
+template <class T>
+struct PkPlan;
+template <>
+struct PkPlan<float> {
+    const uint2 *e;
+    __device__ __forceinline__ void get(int pos, float &a, unsigned int &w) const {
+        const uint2 v = __ldcs(e + pos);
+        a = __uint_as_float(v.x);
+        w = v.y;
+    }
+};
+template <>
+struct PkPlan<double> {
+    const double *a;
+    const unsigned int *w;
+    __device__ __forceinline__ void get(int pos, double &av, unsigned int &wv) const {
+        av = __ldcs(a + pos);
+        wv = __ldcs(w + pos);
+    }
+};
+
+// L consecutive entries (positions pos, pos + 32, ...) of one lane's row:
+// all records first, then the gathers of Y for the first M slots
+template <class T, int L, int M>
+__device__ __forceinline__ void pk_entries(const PkPlan<T> &pl, int pos, int p0,
+                                           const T *__restrict__ Y, T *acc) {
+    T a[L];
+    unsigned int w[L];
+#pragma unroll
+    for (int j = 0; j < L; ++j) pl.get(pos + 32 * j, a[j], w[j]);
+#pragma unroll
+    for (int j = 0; j < L; ++j) {
+        const T *yl = Y + (p0 + ((int)w[j] >> 12));
+#pragma unroll
+        for (int s = 0; s < M; ++s) {
+            const unsigned int q = (w[j] >> (3 * s)) & 7u;
+            if (q < 4u) acc[s] = fmat(a[j], yl[q], acc[s]);
+        }
+    }
+}
+
+template <class T, int M>
+__device__ __forceinline__ void pk_row(const PkPlan<T> &pl, int pos, int len, int p0,
+                                       const T *__restrict__ Y, T *acc) {
+    switch (len) {
+        case 7: pk_entries<T, 7, M>(pl, pos, p0, Y, acc); break;
+        case 6: pk_entries<T, 6, M>(pl, pos, p0, Y, acc); break;
+        case 5: pk_entries<T, 5, M>(pl, pos, p0, Y, acc); break;
+        case 4: pk_entries<T, 4, M>(pl, pos, p0, Y, acc); break;
+        case 8: pk_entries<T, 8, M>(pl, pos, p0, Y, acc); break;
+        default: {
+            int j = 0;
+            for (; j + 4 <= len; j += 4) pk_entries<T, 4, M>(pl, pos + 32 * j, p0, Y, acc);
+            for (; j < len; ++j) pk_entries<T, 1, M>(pl, pos + 32 * j, p0, Y, acc);
+        }
+    }
+}
+
+template <class T>
+__global__ void __launch_bounds__(kBlock)
+k_kprod_k1_pk(int n, const int *__restrict__ sell_ptr, PkPlan<T> pl, const int *__restrict__ Pp,
+              const T *__restrict__ qv, const T *__restrict__ Y, T *__restrict__ out, int project,
+              int dot_mode, DevState *st, double *partials, double *hist, int cap,
+              int check_stop) {
+    if (check_stop && st->stop) return;
+    const int lane = threadIdx.x & 31;
+    const int nslices = (n + 31) >> 5;
+    Dot<T> dot;
+    // the loop is uniform over the warp (one slice per warp and pass)
+    for (int sl = (blockIdx.x * blockDim.x + threadIdx.x) >> 5; sl < nslices;
+         sl += (gridDim.x * blockDim.x) >> 5) {
+        const int i = sl * 32 + lane;
+        const bool row = i < n;  // lanes past the last row take no entries
+        const int base = sell_ptr[sl];
+        const int len = row ? (sell_ptr[sl + 1] - base) >> 5 : 0;
+        int p0 = 0, m = 0;
+        if (row) {
+            p0 = Pp[i];
+            m = Pp[i + 1] - p0;
+        }
+        const unsigned int mw = __reduce_max_sync(0xffffffffu, (unsigned int)m);
+        T q[4], yown[4];
+#pragma unroll
+        for (int s = 0; s < 4; ++s) {
+            const bool h = s < m;
+            q[s] = (h && project) ? __ldcs(qv + p0 + s) : T(0);
+            yown[s] = (h && dot_mode) ? Y[p0 + s] : T(0);
+        }
+        T x[4] = {T(0), T(0), T(0), T(0)};
+        const int pos = base + lane;
+        switch (mw) {
+            case 0: break;  // no row of the slice has an entry of P
+            case 1: pk_row<T, 1>(pl, pos, len, p0, Y, x); break;
+            case 2: pk_row<T, 2>(pl, pos, len, p0, Y, x); break;
+            case 3: pk_row<T, 3>(pl, pos, len, p0, Y, x); break;
+            default: pk_row<T, 4>(pl, pos, len, p0, Y, x); break;
+        }
+        if (project) {
+            T t = T(0);
+#pragma unroll
+            for (int s = 0; s < 4; ++s) t = fmat(q[s], x[s], t);
+#pragma unroll
+            for (int s = 0; s < 4; ++s) x[s] = fmat(-q[s], t, x[s]);
+        }
+#pragma unroll
+        for (int s = 0; s < 4; ++s)
+            if (s < m) {
+                out[p0 + s] = x[s];
+                if (dot_mode) dot.add(yown[s], x[s]);
+            }
+    }
+    if (dot_mode) {
+        __shared__ double sh[32];
+        double bt = block_dot_total(dot, sh);
+        double total;
+        if (grid_reduce(bt, partials, &st->ticket[0], &total)) {
+            if (dot_mode == DOT_ALPHA) finalize_alpha(st, total, hist, cap);
+            else st->aux = total;
+        }
+    }
+}
+
 // k = 1 stand-alone x = scale * (x - q (q^T x)), one thread per row.
 template <class T>
 __global__ void __launch_bounds__(kBlock)
@@ -657,7 +790,21 @@ void launch_kprod(const Launch &L, const Ops<T> &o, const T *Y, T *out, int proj
         launch_kprod_blk<T>(L, o, Y, out, project, dot_mode, w, check_stop);
         return;
     }
-    if (o.k == 1 && o.sell_ptr && o.sa && o.qv && o.maxrow <= 4) {
+    if (o.k == 1 && o.sell_ptr && o.sw && o.qv && o.maxrow <= 4 &&
+        (sizeof(T) == 4 ? o.spk != nullptr : o.sa != nullptr)) {
+        PkPlan<T> pl;
+        if constexpr (sizeof(T) == 4) {
+            pl.e = o.spk;
+        } else {
+            pl.a = o.sa;
+            pl.w = o.sw;
+        }
+        const long long warps = (o.n + 31) / 32;
+        const int g = grid_for(warps * 32, sizeof(T) == 4 ? L.grid_pk32 : L.grid_pk64);
+        k_kprod_k1_pk<T><<<g, kBlock, 0, L.stream>>>(o.n, o.sell_ptr, pl, o.Pp, o.qv, Y, out,
+                                                      project, dot_mode, w.st, w.partials, w.hist,
+                                                      w.hist_cap, check_stop);
+    } else if (o.k == 1 && o.sell_ptr && o.sa && o.qv && o.maxrow <= 4) {
         if constexpr (sizeof(T) == 4) {
             // one block per group of 8 slices, at most the resident grid
             const long long groups = ((o.n + 31) / 32 + kStageWarps - 1) / kStageWarps;
@@ -739,6 +886,19 @@ int staged_blocks_per_sm() {
     int nb = 0;
     if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&nb, k_kprod_k1_staged, kBlock, 0) !=
         cudaSuccess) {
+        cudaGetLastError();
+        nb = 1;
+    }
+    return nb > 0 ? nb : 1;
+}
+
+int pk_blocks_per_sm(int double_precision) {
+    int nb = 0;
+    const cudaError_t e =
+        double_precision
+            ? cudaOccupancyMaxActiveBlocksPerMultiprocessor(&nb, k_kprod_k1_pk<double>, kBlock, 0)
+            : cudaOccupancyMaxActiveBlocksPerMultiprocessor(&nb, k_kprod_k1_pk<float>, kBlock, 0);
+    if (e != cudaSuccess) {
         cudaGetLastError();
         nb = 1;
     }

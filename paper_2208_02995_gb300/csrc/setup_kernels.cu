@@ -407,11 +407,15 @@ __global__ void k_sell_len(int n, const int *__restrict__ Ap, int *slen) {
 // in row l (3 bits, 7 if absent).  Padding entries carry no slot (map 0xFFF)
 // and offset 0; that includes every entry of the lanes past row n - 1 in a
 // ragged last slice, so that no entry of the plan is left unwritten.
-// Requires rows of P with at most 4 entries.
+// The packed word of an entry (sw, optional) holds the offset relative to
+// the entry's own row, (o - p0_i) << 12 | map, and *wide is set if some
+// difference falls outside [-2^19, 2^19).  Requires rows of P with at most
+// 4 entries.
 __global__ void k_sell_plan(int n, const int *__restrict__ Ap, const int *__restrict__ Aj,
                             const int *__restrict__ Pp, const int *__restrict__ Pj,
                             const int *__restrict__ sell_ptr, int *soff, unsigned short *smap,
-                            int *dpos) {
+                            unsigned int *sw, int *wide, int *dpos) {
+    int too_wide = 0;
     const int nlanes = ((n + 31) >> 5) << 5;
     for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < nlanes; i += gridDim.x * blockDim.x) {
         const int sl = i >> 5, lane = i & 31;
@@ -443,8 +447,14 @@ __global__ void k_sell_plan(int n, const int *__restrict__ Ap, const int *__rest
             }
             soff[pos] = off;
             smap[pos] = (unsigned short)map;
+            if (sw) {
+                const int rel = (j < rl) ? off - p0 : 0;
+                if (rel < -(1 << 19) || rel >= (1 << 19)) too_wide = 1;
+                sw[pos] = ((unsigned int)rel << 12) | map;
+            }
         }
     }
+    if (__any_sync(0xffffffffu, too_wide) && (threadIdx.x & 31) == 0) atomicOr(wide, 1);
 }
 
 // A^ = D^{-1/2} A D^{-1/2} in SELL-32 order (padding 0).  One warp per
@@ -454,7 +464,8 @@ template <class T>
 __global__ void __launch_bounds__(kBlock)
 k_sell_values(int n, const int *__restrict__ Ap, const int *__restrict__ Aj,
               const double *__restrict__ Av, const double *__restrict__ dsq,
-              const int *__restrict__ sell_ptr, T *sa) {
+              const int *__restrict__ sell_ptr, T *sa, const unsigned int *__restrict__ sw,
+              uint2 *spk) {
     constexpr int CAP = 256;
     __shared__ double sv[kBlock / 32][CAP];
     __shared__ int sc[kBlock / 32][CAP];
@@ -486,7 +497,14 @@ k_sell_values(int n, const int *__restrict__ Ap, const int *__restrict__ Aj,
                 else
                     v = di * a * dsq[l];
             }
-            sa[base + j * 32 + lane] = v;
+            const int pos = base + j * 32 + lane;
+            if constexpr (sizeof(T) == 4) {
+                if (spk) {
+                    spk[pos] = make_uint2(__float_as_uint(v), sw[pos]);
+                    continue;
+                }
+            }
+            sa[pos] = v;
         }
         __syncwarp();
     }
@@ -635,25 +653,28 @@ void launch_sell_len(const Launch &L, int n, const int *Ap, int *slen) {
 
 void launch_sell_plan(const Launch &L, int n, const int *Ap, const int *Aj, const int *Pp,
                       const int *Pj, const int *sell_ptr, int *soff, unsigned short *smap,
-                      int *dpos) {
+                      unsigned int *sw, int *wide, int *dpos) {
     if (n <= 0) return;
     k_sell_plan<<<grid_for(n, L.grid_rows), kBlock, 0, L.stream>>>(n, Ap, Aj, Pp, Pj, sell_ptr,
-                                                                   soff, smap, dpos);
+                                                                   soff, smap, sw, wide, dpos);
     note_launch();
 }
 
 template <class T>
 void launch_sell_values(const Launch &L, int n, const int *Ap, const int *Aj, const double *Av,
-                        const double *dsq, const int *sell_ptr, T *sa) {
+                        const double *dsq, const int *sell_ptr, T *sa, const unsigned int *sw,
+                        uint2 *spk) {
     if (n <= 0) return;
     k_sell_values<T><<<grid_for((long long)((n + 31) / 32) * 32, L.grid_rows), kBlock, 0,
-                       L.stream>>>(n, Ap, Aj, Av, dsq, sell_ptr, sa);
+                       L.stream>>>(n, Ap, Aj, Av, dsq, sell_ptr, sa, sw, spk);
     note_launch();
 }
 template void launch_sell_values<float>(const Launch &, int, const int *, const int *,
-                                        const double *, const double *, const int *, float *);
+                                        const double *, const double *, const int *, float *,
+                                        const unsigned int *, uint2 *);
 template void launch_sell_values<double>(const Launch &, int, const int *, const int *,
-                                         const double *, const double *, const int *, double *);
+                                         const double *, const double *, const int *, double *,
+                                         const unsigned int *, uint2 *);
 
 void launch_diag_scales(const Launch &L, int n, const double *dinv, double *dsq, double *dhalf) {
     if (n <= 0) return;

@@ -27,7 +27,7 @@ import numpy as np
 
 __all__ = [
     "Problem", "splitmix64", "uniform01", "normal",
-    "poisson2d", "diffusion3d_fv", "aniso3d", "elasticity3d",
+    "poisson2d", "diffusion3d_fv", "ring1d", "aniso3d", "elasticity3d",
     "random_problem", "config", "CONFIG_NAMES",
 ]
 
@@ -230,6 +230,34 @@ def diffusion3d_fv(N: int = 128, agg: int = 3, sigma: float = 2.0, seed: int = 2
     return _scalar_problem(f"fv3d_{N}", dims, nb, ok, vals, agg, iters,
                            {"kind": "fv3d", "N": N, "agg": agg, "sigma": sigma,
                             "seed": seed})
+
+
+def ring1d(n: int = 1000, agg: int = 2, sigma: float = 0.5, seed: int = 3,
+           iters: int = 12) -> Problem:
+    """Periodic 1D chain (a ring): transmissibility T_i = exp(sigma xi_i)
+    between rows i and i + 1 mod n, diagonal T_(i-1) + T_i, so A 1 = 0.  The
+    wrap-around coupling joins the first and the last row, the widest
+    possible distance between coupled rows in this ordering.  k = 1,
+    aggregates of ``agg`` consecutive rows (the remainder joins the last)."""
+    T = np.exp(sigma * normal(seed, n))
+    i = np.arange(n, dtype=np.int64)
+    nb = np.stack([(i - 1) % n, i, (i + 1) % n], axis=1)
+    vals = np.stack([-T[(i - 1) % n], T[(i - 1) % n] + T, -T], axis=1)
+    order = np.argsort(nb, axis=1, kind="stable")  # ascending columns per row
+    nb = np.take_along_axis(nb, order, axis=1)
+    vals = np.take_along_axis(vals, order, axis=1)
+    ok = np.ones(nb.shape, dtype=bool)
+    A_rowptr, A_col, A_val = _csr_from_dense_slots(nb, vals, ok)
+    nc = n // agg
+    node_agg = _agg_index(i, agg, n)
+    size = np.bincount(node_agg, minlength=nc).astype(np.float64)
+    g, keep = _pattern_from_neighbours(nb, ok, node_agg)
+    P_rowptr, P_col, _ = _csr_from_dense_slots(g, None, keep)
+    rows = np.repeat(i, np.diff(P_rowptr))
+    P0_val = np.where(P_col == node_agg[rows], 1.0 / np.sqrt(size[P_col]), 0.0)
+    return Problem(f"ring1d_{n}", n, int(nc), 1, A_rowptr, A_col, A_val, P_rowptr, P_col,
+                   P0_val, np.ones((n, 1)), np.sqrt(size)[:, None].copy(), iters,
+                   {"kind": "ring1d", "n": n, "agg": agg, "sigma": sigma, "seed": seed})
 
 
 def aniso3d(N: int = 160, eps: float = 1e-3, agg: int = 2, iters: int = 15) -> Problem:

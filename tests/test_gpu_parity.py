@@ -40,6 +40,7 @@ SMALL = [
     I.diffusion3d_fv(21, 3),                  # ragged aggregates (21 = 7*3)
     I.diffusion3d_fv(23, 3),                  # remainder aggregate 5 wide
     I.aniso3d(14, 1e-3, 2),
+    I.ring1d(1001, 2),                        # wrap-around coupling, remainder aggregate 3
     I.elasticity3d(7, 0.3, 3),                # 6 rigid-body modes, rows up to 48
     I.elasticity3d(8, 0.25, 3, 1.5, 5),
     I.random_problem(300, 60, 1, seed=1, wide_rows=(3, 77), wide=40),
@@ -284,6 +285,34 @@ def test_workload2_full_size(precision):
         Eref = o.energy(ref["P"])
         assert abs(c.energy() - Eref) <= MIXED_E_TOL * abs(Eref)
         assert relf(P, ref["P"]) <= 1e-4
+    assert o.constraint_error(P) <= CONSTRAINT_TOL
+
+
+@pytest.mark.parametrize("precision", ["fp64", "mixed"])
+def test_wide_offsets_plain_plan(precision):
+    """A ring of 400,000 rows (nnz(P) = 800,000): the wrap-around coupling of
+    the first and the last row puts row l of P about 800,000 entries away
+    from row i, beyond the 20-bit relative offsets of the packed plan, so
+    the plain SELL-32 plan (absolute offsets) serves this pattern.  Masked
+    products element-wise, then 12 iterations against the oracle."""
+    prob = I.ring1d(400_000, 2)
+    assert prob.nnz_p > (1 << 19) + 2
+    o = Oracle(prob)
+    c = ctx(prob, precision)
+    X = np.random.default_rng(5).standard_normal(prob.nnz_p)
+    tol = KPROD_TOL if precision == "fp64" else 2e-6
+    ref = o.project(o.kprod(X))
+    got = c.kprod(X, project=True)
+    assert np.abs(got - ref).max() <= tol * np.abs(ref).max()
+    ref = o.minimize(12, 0.0)
+    done, _ = c.iterate(12, 0.0)
+    assert done == ref["applied"]
+    P = c.get_p()
+    if precision == "fp64":
+        assert relf(P, ref["P"]) <= FP64_TOL
+    else:
+        Eref = o.energy(ref["P"])
+        assert abs(c.energy() - Eref) <= MIXED_E_TOL * abs(Eref)
     assert o.constraint_error(P) <= CONSTRAINT_TOL
 
 

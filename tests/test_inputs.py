@@ -56,7 +56,7 @@ def test_config_sizes(cfg):
 @pytest.mark.parametrize("prob", [
     I.poisson2d(12, 2), I.diffusion3d_fv(8, 3), I.aniso3d(6, 1e-3, 2),
     I.elasticity3d(5, 0.3, 2), I.elasticity3d(6, 0.25, 3, 1.5, 5),
-    I.random_problem(40, 12, 2, seed=3),
+    I.random_problem(40, 12, 2, seed=3), I.ring1d(41, 2),
 ], ids=lambda p: p.name)
 def test_structure(prob):
     A = _A(prob)
@@ -94,6 +94,9 @@ def test_neumann_kernels():
     assert np.abs(AB).max() < 1e-12 * np.abs(el.A_val).max()
     het = I.elasticity3d(6, 0.25, 3, 1.5, 5)
     assert np.abs(_A(het) @ het.B).max() < 1e-12 * np.abs(het.A_val).max()
+    ring = I.ring1d(41, 2)
+    assert np.abs(_A(ring) @ np.ones(ring.n)).max() < 1e-14 * np.abs(ring.A_val).max()
+    assert _A(ring)[0, ring.n - 1] != 0  # the wrap-around coupling
 
 
 def test_elasticity_blocks():
