@@ -37,7 +37,7 @@ if ROOT not in sys.path:
 KERNEL_SOURCES = ["paper_2208_02995_gb300/csrc/iter_kernels.cu",
                   "paper_2208_02995_gb300/csrc/device_util.cuh",
                   "paper_2208_02995_gb300/csrc/emin_internal.cuh"]
-PROFILE = "profiles/kprod_k1_staged_fv3d128.md"
+PROFILE = "profiles/kprod_k1_pk_fv3d128.md"
 
 METRIC = ("restricted-PCG iterations/s and masked A·P effective HBM GB/s "
           "(% of peak), FP32 vs FP64")
