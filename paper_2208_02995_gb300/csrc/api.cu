@@ -669,6 +669,7 @@ int emin_create(emin_ctx **out, int n, int nc, int k, const int *A_rowptr, const
     occ_rows = 8;   // 2048 resident threads per SM at 256 threads per block
     occ_warps = 8;
     c->L.stream = c->stream;
+    c->L.nsm = nsm;
     c->L.grid_rows = nsm * occ_rows;
     c->L.grid_warps = nsm * occ_warps;
     if (c->L.grid_rows > kMaxGrid) c->L.grid_rows = kMaxGrid;

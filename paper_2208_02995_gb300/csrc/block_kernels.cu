@@ -280,8 +280,8 @@ struct Pair<double> {
     using V = double2;
 };
 
-template <class T>
-__global__ void __launch_bounds__(kBlock)
+template <class T, int MINB>
+__global__ void __launch_bounds__(kBlock, MINB)
 k_kprod_blk2(int ntiles, const int *__restrict__ tile_map, const int *__restrict__ Ap,
              const T *__restrict__ Av, const int *__restrict__ Pp, const int *__restrict__ Pj,
              const int *__restrict__ boff, const unsigned short *__restrict__ blen,
@@ -346,59 +346,79 @@ k_kprod_blk2(int ntiles, const int *__restrict__ tile_map, const int *__restrict
             }
         }
         if (project) {
-            // B_i restricted to this block's columns: the rows c0..c0+5 of B_c
-            T bc[KB][KB];
-#pragma unroll
-            for (int t = 0; t < KB; ++t)
-#pragma unroll
-                for (int a = 0; a < KB; ++a) bc[t][a] = valid ? Bc[(size_t)(c0 + t) * KB + a] : T(0);
-            // this block's share of t_r = B_i^T x_r, then the sum over the node's lanes
+            // B_i restricted to this block's columns is rows c0..c0+5 of B_c;
+            // they are streamed one row at a time (L1-resident) rather than
+            // held, which keeps the epilogue's register footprint near that
+            // of the accumulators.  This block's share of t_r = B_i^T x_r:
+            const T *bcp = Bc + (size_t)c0 * KB;
+            T tr[NB][KB];
 #pragma unroll
             for (int r = 0; r < NB; ++r)
 #pragma unroll
-                for (int a = 0; a < KB; ++a) {
-                    T v2 = T(0);
+                for (int a = 0; a < KB; ++a) tr[r][a] = T(0);
+            if (valid) {
 #pragma unroll
-                    for (int t = 0; t < KB; ++t) v2 = fmat(bc[t][a], acc[r][t], v2);
-                    sT[w][lane][r * KB + a] = v2;
+                for (int t = 0; t < KB; ++t) {
+                    T b[KB];
+#pragma unroll
+                    for (int a = 0; a < KB; ++a) b[a] = bcp[t * KB + a];
+#pragma unroll
+                    for (int r = 0; r < NB; ++r)
+#pragma unroll
+                        for (int a = 0; a < KB; ++a) tr[r][a] = fmat(b[a], acc[r][t], tr[r][a]);
                 }
-            __syncwarp();
-            // the node's lanes are consecutive: first lane = lane - s
-            const int first = lane - s;
-            T tv[NB][KB];
+            }
 #pragma unroll
             for (int r = 0; r < NB; ++r)
 #pragma unroll
-                for (int a = 0; a < KB; ++a) tv[r][a] = T(0);
+                for (int a = 0; a < KB; ++a) sT[w][lane][r * KB + a] = tr[r][a];
+            __syncwarp();
+            // the sum over the node's lanes (consecutive: first lane = lane - s)
+            const int first = lane - s;
+#pragma unroll
+            for (int r = 0; r < NB; ++r)
+#pragma unroll
+                for (int a = 0; a < KB; ++a) tr[r][a] = T(0);
             if (valid) {
                 const int nslot = mrow / KB;
                 for (int u = 0; u < nslot; ++u)
 #pragma unroll
                     for (int r = 0; r < NB; ++r)
 #pragma unroll
-                        for (int a = 0; a < KB; ++a) tv[r][a] += sT[w][first + u][r * KB + a];
+                        for (int a = 0; a < KB; ++a) tr[r][a] += sT[w][first + u][r * KB + a];
             }
             __syncwarp();
-            // c_r = G^{-1} t_r (the node's three rows share J_i, hence G_i)
-            T g[KK];
+            if (valid) {
+                // c_r = G^{-1} t_r (the node's three rows share J_i, hence G_i),
+                // overwriting t_r row by row
+                const T *gp = Ginv + (size_t)NB * v * KK;
 #pragma unroll
-            for (int e = 0; e < KK; ++e) g[e] = valid ? Ginv[(size_t)NB * v * KK + e] : T(0);
+                for (int r = 0; r < NB; ++r) {
+                    T cv[KB];
 #pragma unroll
-            for (int r = 0; r < NB; ++r) {
-                T cv[KB];
+                    for (int a = 0; a < KB; ++a) {
+                        T v2 = T(0);
 #pragma unroll
-                for (int a = 0; a < KB; ++a) {
-                    T v2 = T(0);
+                        for (int c = 0; c < KB; ++c)
+                            v2 = fmat(gp[a >= c ? tri(a, c) : tri(c, a)], tr[r][c], v2);
+                        cv[a] = v2;
+                    }
 #pragma unroll
-                    for (int c = 0; c < KB; ++c) v2 = fmat(g[a >= c ? tri(a, c) : tri(c, a)], tv[r][c], v2);
-                    cv[a] = v2;
+                    for (int a = 0; a < KB; ++a) tr[r][a] = cv[a];
                 }
+                // x_r -= B_i c_r, streaming the rows of B_i again
 #pragma unroll
                 for (int t = 0; t < KB; ++t) {
-                    T x = acc[r][t];
+                    T b[KB];
 #pragma unroll
-                    for (int a = 0; a < KB; ++a) x = fmat(-bc[t][a], cv[a], x);
-                    acc[r][t] = x;
+                    for (int a = 0; a < KB; ++a) b[a] = bcp[t * KB + a];
+#pragma unroll
+                    for (int r = 0; r < NB; ++r) {
+                        T x = acc[r][t];
+#pragma unroll
+                        for (int a = 0; a < KB; ++a) x = fmat(-b[a], tr[r][a], x);
+                        acc[r][t] = x;
+                    }
                 }
             }
         }
@@ -467,17 +487,37 @@ void launch_node_slots(const Launch &L, int n, const int *Pp, int *na) {
     note_launch();
 }
 
+// the output-block kernel on its resident grid (blocks per SM from the
+// occupancy of this instantiation), at most one tile per warp
+template <class T, int MINB>
+void launch_blk2(const Launch &L, const Ops<T> &o, const T *Y, T *out, int project, int dot_mode,
+                 Work<T> &w, int check_stop) {
+    static const int per_sm = [] {
+        int nb = 0;
+        if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&nb, k_kprod_blk2<T, MINB>, kBlock, 0) !=
+            cudaSuccess) {
+            cudaGetLastError();
+            nb = 1;
+        }
+        return nb > 0 ? nb : 1;
+    }();
+    long long cap = (long long)L.nsm * per_sm;
+    if (cap > kMaxGrid) cap = kMaxGrid;
+    const int g = grid_for((long long)o.ntiles * 32, (int)cap);
+    k_kprod_blk2<T, MINB><<<g, kBlock, 0, L.stream>>>(o.ntiles, o.tile_map, o.Ap, o.Av, o.Pp, o.Pj,
+                                                       o.boff, o.blen, o.bmap, o.Bc, o.Ginv, Y, out,
+                                                       project, dot_mode, w.st, w.partials, w.hist,
+                                                       w.hist_cap, check_stop);
+}
+
 template <class T>
 void launch_kprod_blk(const Launch &L, const Ops<T> &o, const T *Y, T *out, int project,
                       int dot_mode, Work<T> &w, int check_stop) {
     const int nn = o.n / NB;
     if (nn <= 0) return;
     if (o.tile_map && o.ntiles > 0) {
-        const int g = grid_for((long long)o.ntiles * 32, L.grid_warps);
-        k_kprod_blk2<T><<<g, kBlock, 0, L.stream>>>(o.ntiles, o.tile_map, o.Ap, o.Av, o.Pp, o.Pj,
-                                                     o.boff, o.blen, o.bmap, o.Bc, o.Ginv, Y, out,
-                                                     project, dot_mode, w.st, w.partials, w.hist,
-                                                     w.hist_cap, check_stop);
+        // register caps without spills: 80 per thread (float), 128 (double)
+        launch_blk2<T, sizeof(T) == 4 ? 3 : 2>(L, o, Y, out, project, dot_mode, w, check_stop);
         note_launch();
         return;
     }

@@ -117,6 +117,7 @@ struct Launch {
     int grid_rows;    // grid of thread-per-row kernels
     int grid_warps;   // grid of warp-per-row kernels
     int grid_staged;  // resident grid of the staged masked product
+    int nsm;          // streaming multiprocessors of the device
     int grid_pk32;    // resident grids of the packed-plan masked product (float, double)
     int grid_pk64;
 };

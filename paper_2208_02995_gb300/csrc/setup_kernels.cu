@@ -329,7 +329,18 @@ __global__ void k_setup_k1(int n, const int *__restrict__ dpos, const double *__
 #pragma unroll
         for (int s = 0; s < 4; ++s) G = fma(b[s], b[s], G);
         double r = 0.0, gi = 0.0;
-        if (G > 0.0) {
+        if (sizeof(Tit) == 4 && G >= 1e-30 && G <= 1e30) {
+            // float path: q = b / |b| is stored in float, so 1/|b| is taken in
+            // float; 1/G (for the least-norm correction and the final FP64
+            // restore) by two Newton-Raphson steps for the reciprocal,
+            // x <- x + x (1 - G x), from the float seed 1/|b|^2, each step
+            // squaring the relative error (about 1e-7 -> 1e-14 -> 1e-28)
+            const float rf = rsqrtf((float)G);
+            r = (double)rf;
+            gi = (double)(rf * rf);
+            gi = fma(gi, fma(-G, gi, 1.0), gi);
+            gi = fma(gi, fma(-G, gi, 1.0), gi);
+        } else if (G > 0.0) {
             r = rsqrt_newton(G);
             gi = r * r;
         } else if (policy == EMIN_RANK_PINV) {

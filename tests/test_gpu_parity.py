@@ -66,9 +66,12 @@ def test_kprod_matches_oracle(prob, precision):
 
 
 @pytest.mark.parametrize("prob", SMALL, ids=SMALL_IDS)
-def test_setup_matches_oracle(prob):
+@pytest.mark.parametrize("precision", ["fp64", "mixed"])
+def test_setup_matches_oracle(prob, precision):
+    """Corrected P0 (Algorithm 2) in both precisions: the mixed set-up keeps
+    the Gram inverse and the least-norm correction in FP64."""
     o = Oracle(prob)
-    c = ctx(prob)
+    c = ctx(prob, precision)
     P = c.get_p()
     assert np.abs(P - o.P0).max() <= 1e-13 * max(1.0, np.abs(o.P0).max())
     assert o.constraint_error(P) <= CONSTRAINT_TOL
