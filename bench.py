@@ -54,6 +54,7 @@ def parse():
     ap.add_argument("--impl", choices=["ours", "reference"], default="ours")
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-e2e", action="store_true")
+    ap.add_argument("--no-tau", action="store_true", help="skip the time-to-tau measurement")
     ap.add_argument("--precision", choices=["both", "mixed", "fp64"], default="both",
                     help="profiling aid: run one arm only (the JSON line needs both)")
     ap.add_argument("--workload", type=int, default=WORKLOAD,
@@ -356,7 +357,7 @@ def run_ours(args, dist):
             "ms_per_step": f["ms"] / K,
             "dtype": "f64",
             "roofline": {
-                "kernel": "masked product + projection + y^T y_ (k_kprod_k1_sell<double>)",
+                "kernel": "masked product + projection + y^T y_ (k_kprod_k1_pk<double>, packed SELL-32 plan)",
                 "bound": "alu",
                 "achieved": ach64,
                 "peak": FP64_PEAK_TFLOPS,
@@ -380,9 +381,55 @@ def run_ours(args, dist):
             "time_to_P_ratio": f["ms"] / m["ms"],
         },
     }
+    if not args.no_tau:
+        line["time_to_tau"] = time_to_tau(prob, stream)
     if dist.world == 1 and not args.no_cpu_baseline and dist.rank == 0:
         line["cpu_baseline"] = cpu_baseline(prob)
     return line
+
+
+TAUS = (0.1, 1e-3, 1e-6)
+TAU_MAXIT = 200
+
+
+def time_to_tau(prob, stream, reps=5, warm=2):
+    """Time to the energy stop test of Eq. (relRed): one whole minimisation
+    (set-up, iterations until dE_k < tau dE_1 with at most TAU_MAXIT, P) per
+    sample, CUDA events on the library's stream, for the paper's default
+    tau = 0.1 and two tighter ones, in both precisions."""
+    import torch
+
+    from paper_2208_02995_gb300.emin import Context
+    out = {"maxit": TAU_MAXIT, "unit": "ms per minimisation (set-up + iterations to the "
+           "stop test + P), mean of 5 after 2 warm-up", "samples": reps}
+    for prec in ("mixed", "fp64"):
+        with torch.cuda.stream(stream):
+            ctx = Context(prob, precision=prec, stream=stream)
+            P = torch.empty(prob.nnz_p, dtype=torch.float64, device="cuda")
+        rows = []
+        for tau in TAUS:
+            done = [0]
+
+            def step():
+                ctx.reset()
+                done[0] = ctx.iterate(TAU_MAXIT, tau)[0]
+                ctx.get_p(P)
+
+            for _ in range(warm):
+                step()
+            torch.cuda.synchronize()
+            t0 = torch.cuda.Event(enable_timing=True)
+            t1 = torch.cuda.Event(enable_timing=True)
+            t0.record(stream)
+            for _ in range(reps):
+                step()
+            t1.record(stream)
+            torch.cuda.synchronize()
+            rows.append({"tau": tau, "iterations": int(done[0]),
+                         "ms": t0.elapsed_time(t1) / reps})
+        out[prec] = rows
+        ctx.close()
+    return out
 
 
 def run_e2e(prob, args, dist):

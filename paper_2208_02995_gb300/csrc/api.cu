@@ -532,10 +532,51 @@ bool capturable(cudaStream_t s) {
     return s != nullptr && s != cudaStreamLegacy && s != cudaStreamPerThread;
 }
 
+// One iteration as the body of a conditional while node (captured once per
+// workspace): the loop control at the end of the body keeps it running while
+// iterations of the call are left and the stop test of Eq. (relRed) has not
+// fired, so a call stops launching work as soon as the energy criterion is met.
+template <class T>
+void build_while_graph(emin_ctx *c, const Ops<T> &o, Work<T> &w) {
+    cudaGraph_t graph = nullptr;
+    if (cudaGraphCreate(&graph, 0) != cudaSuccess) {
+        cudaGetLastError();
+        return;
+    }
+    cudaGraphConditionalHandle h;
+    bool ok = cudaGraphConditionalHandleCreate(&h, graph, 1, cudaGraphCondAssignDefault) ==
+              cudaSuccess;
+    cudaGraphNodeParams p = {};
+    if (ok) {
+        p.type = cudaGraphNodeTypeConditional;
+        p.conditional.handle = h;
+        p.conditional.type = cudaGraphCondTypeWhile;
+        p.conditional.size = 1;
+        cudaGraphNode_t node;
+        ok = cudaGraphAddNode(&node, graph, nullptr, nullptr, 0, &p) == cudaSuccess;
+    }
+    if (ok) {
+        cudaGraph_t body = p.conditional.phGraph_out[0];
+        const long long before = launches_so_far();
+        ok = cudaStreamBeginCaptureToGraph(c->stream, body, nullptr, nullptr, 0,
+                                           cudaStreamCaptureModeThreadLocal) == cudaSuccess;
+        if (ok) {
+            launch_iterations<T>(c, o, w, 1, false);
+            launch_loop_control(c->L, w.st, h);
+            cudaGraph_t captured = nullptr;
+            ok = cudaStreamEndCapture(c->stream, &captured) == cudaSuccess;
+        }
+        note_launches(before - launches_so_far());  // captured, not run
+    }
+    if (ok && cudaGraphInstantiate(&w.gwhile, graph, 0) != cudaSuccess) w.gwhile = nullptr;
+    cudaGraphDestroy(graph);
+    cudaGetLastError();
+}
+
 template <class T>
 int iterate_impl(emin_ctx *c, const Ops<T> &o, Work<T> &w, int n_iters, double tol,
                  bool timed = false) {
-    launch_state_begin(c->L, w.st, tol);
+    launch_state_begin(c->L, w.st, tol, n_iters);
     timed = timed && c->timing > 0 && o.n > 0;
     if (timed) {
         const size_t need = (size_t)n_iters * 2;
@@ -545,9 +586,15 @@ int iterate_impl(emin_ctx *c, const Ops<T> &o, Work<T> &w, int n_iters, double t
             c->events.push_back(e);
         }
     }
-    bool launched = false;
-    if (n_iters > 0 && o.n > 0 && capturable(c->stream)) {
-        // the whole loop as one CUDA graph, captured once per (count, timing)
+    bool launched = false, looped = false;
+    if (n_iters > 0 && o.n > 0 && capturable(c->stream) && !timed) {
+        if (!w.gwhile) build_while_graph<T>(c, o, w);
+        if (w.gwhile && cudaGraphLaunch(w.gwhile, c->stream) == cudaSuccess) launched = looped = true;
+        cudaGetLastError();
+    }
+    if (!launched && n_iters > 0 && o.n > 0 && capturable(c->stream)) {
+        // the whole loop unrolled into one CUDA graph, captured once per
+        // (count, timing): the timed runs bracket single launches with events
         const int tkey = timed ? c->timing : 0;
         if (!(w.gexec && w.gn == n_iters && w.gtimed == tkey)) {
             if (w.gexec) {
@@ -577,6 +624,7 @@ int iterate_impl(emin_ctx *c, const Ops<T> &o, Work<T> &w, int n_iters, double t
     if (!launched) EMIN_TRY(launch_iterations<T>(c, o, w, n_iters, timed));
     EMIN_TRY(check_launch());
     EMIN_TRY(read_state(c, w.st));
+    if (looped) note_launches(4LL * (n_iters - c->hstate->loop_left));  // passes x 4 kernels
     if (timed) {
         for (int it = 0; it < n_iters; it += c->timing) {
             float ms = 0.f;
@@ -630,6 +678,8 @@ void emin_destroy(emin_ctx *c) {
         for (cudaGraphExec_t g : {c->w64.gexec, c->adj.gexec, c->aux.gexec})
             if (g) cudaGraphExecDestroy(g);
         if (c->w32.gexec) cudaGraphExecDestroy(c->w32.gexec);
+        for (cudaGraphExec_t g : {c->w64.gwhile, c->adj.gwhile, c->aux.gwhile, c->w32.gwhile})
+            if (g) cudaGraphExecDestroy(g);
         for (void *p : c->dev_allocs) cudaFree(p);
         for (cudaEvent_t e : c->events) cudaEventDestroy(e);
         if (c->hstate) cudaFreeHost(c->hstate);

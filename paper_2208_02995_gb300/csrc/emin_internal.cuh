@@ -53,6 +53,7 @@ struct DevState {
     int applied;         // steps applied since (re)start
     int stop;            // 0 running, 1 converged, 2 error
     int status;          // emin_status of a device-detected error
+    int loop_left;       // iterations left in the current call (graph while-loop)
     unsigned int ticket[4];
 };
 
@@ -72,6 +73,9 @@ struct Work {
     // the captured iteration loop (CUDA graph) for gn iterations
     cudaGraphExec_t gexec = nullptr;
     int gn = -1, gtimed = -1;
+    // one iteration as the body of a conditional while node: runs until the
+    // call's count is used up or the stop test fires, for any count
+    cudaGraphExec_t gwhile = nullptr;
 };
 
 // Everything a masked-product launch needs to know about the problem.
@@ -203,7 +207,9 @@ void set_iter_attributes();
 int staged_blocks_per_sm();
 int pk_blocks_per_sm(int double_precision);
 void set_adjoint_attributes();
-void launch_state_begin(const Launch &L, DevState *st, double tau);
+void launch_state_begin(const Launch &L, DevState *st, double tau, int n_iters);
+// the while-loop control of the captured iteration graph (one thread)
+void launch_loop_control(const Launch &L, DevState *st, cudaGraphConditionalHandle h);
 
 // ---- node-block kernels (block_kernels.cu) ----
 // returns 1 if it launched the structure test (flag in *bad), 0 if the

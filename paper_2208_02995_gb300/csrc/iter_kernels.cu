@@ -772,7 +772,19 @@ __global__ void k_state_reset(DevState *st) {
     *st = z;
 }
 
-__global__ void k_state_begin(DevState *st, double tau) { st->tau = tau; }
+__global__ void k_state_begin(DevState *st, double tau, int n_iters) {
+    st->tau = tau;
+    st->loop_left = n_iters;
+}
+
+// End of one iteration of the captured while-loop: one iteration fewer
+// left; the loop goes on while some are left and the stop test has not
+// fired (a stopped state makes every kernel of the body return at once, so
+// at most one empty pass follows the stop).
+__global__ void k_loop_control(DevState *st, cudaGraphConditionalHandle h) {
+    const int left = --st->loop_left;
+    cudaGraphSetConditional(h, (left > 0 && st->stop == 0) ? 1u : 0u);
+}
 
 inline int grid_for(long long work, int cap) {
     long long g = (work + kBlock - 1) / kBlock;
@@ -916,8 +928,13 @@ void launch_state_reset(const Launch &L, DevState *st) {
     note_launch();
 }
 
-void launch_state_begin(const Launch &L, DevState *st, double tau) {
-    k_state_begin<<<1, 1, 0, L.stream>>>(st, tau);
+void launch_loop_control(const Launch &L, DevState *st, cudaGraphConditionalHandle h) {
+    k_loop_control<<<1, 1, 0, L.stream>>>(st, h);
+    note_launch();
+}
+
+void launch_state_begin(const Launch &L, DevState *st, double tau, int n_iters) {
+    k_state_begin<<<1, 1, 0, L.stream>>>(st, tau, n_iters);
     note_launch();
 }
 

@@ -320,6 +320,66 @@ def test_wide_offsets_plain_plan(precision):
 
 
 @pytest.mark.parametrize("precision", ["fp64", "mixed"])
+@pytest.mark.parametrize("tau", [0.0, 0.05])
+def test_while_graph_matches_direct_launches(precision, tau):
+    """Untimed calls on a non-default stream run one captured iteration as
+    the body of a conditional while node, which stops as soon as the stop
+    test fires: bit-identical to direct launches on the legacy stream, and
+    the launch count is the state set-up plus 4 kernels per pass (ydir,
+    masked product, update, loop control)."""
+    import torch
+    from paper_2208_02995_gb300.emin import Context, emin_timing
+    prob = I.diffusion3d_fv(20, 3)
+    a = ctx(prob, precision)
+    da, _ = a.iterate(40, tau)
+    s = torch.cuda.Stream()
+    b = Context(prob, precision=precision, stream=s)
+    l0 = emin_timing(b.h)["total_launches"]
+    db, _ = b.iterate(40, tau)
+    l1 = emin_timing(b.h)["total_launches"]
+    assert db == da
+    assert np.array_equal(a.get_p(), b.get_p())
+    if tau > 0.0:
+        assert db < 40
+    if db == 40:
+        assert l1 - l0 == 1 + 4 * 40
+    else:
+        # stopped early: by the energy test in the masked product (the step
+        # is not applied: one pass more than the applied steps) or by the
+        # convergence floor of gamma in the update (the pass that applied the
+        # last step ends the loop)
+        assert l1 - l0 in (1 + 4 * db, 1 + 4 * (db + 1))
+    # a converged context: the next call runs one empty pass and applies nothing
+    if tau > 0.0:
+        l2 = emin_timing(b.h)["total_launches"]
+        assert b.iterate(10, tau)[0] == 0
+        assert emin_timing(b.h)["total_launches"] - l2 == 1 + 4
+        assert np.array_equal(a.get_p(), b.get_p())
+
+
+@pytest.mark.parametrize("precision", ["fp64", "mixed"])
+@pytest.mark.parametrize("tau", [0.1, 1e-3])
+def test_workload2_energy_stop(precision, tau):
+    """The paper's default stop test (tau = 0.1) and a tighter one on the
+    full 128^3 workload: the same number of applied steps as the oracle, P
+    (FP64) or the energy (mixed) at the oracle's bar."""
+    prob = I.config(2)
+    o = Oracle(prob)
+    ref = o.minimize(200, tau)
+    c = ctx(prob, precision)
+    done, rel = c.iterate(200, tau)
+    assert done == ref["applied"] < 200
+    assert rel < tau
+    P = c.get_p()
+    if precision == "fp64":
+        assert relf(P, ref["P"]) <= FP64_TOL
+    else:
+        Eref = o.energy(ref["P"])
+        assert abs(c.energy() - Eref) <= MIXED_E_TOL * abs(Eref)
+    assert o.constraint_error(P) <= CONSTRAINT_TOL
+
+
+@pytest.mark.parametrize("precision", ["fp64", "mixed"])
 def test_graph_replay_matches_direct_launches(precision):
     """On a non-default stream the iteration loop runs as a captured CUDA
     graph (with the kernel timing events inside); the result is bit-identical
