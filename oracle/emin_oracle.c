@@ -10,7 +10,10 @@
  * Gram/Cholesky factorisation, it forms the masked product by computing a
  * full row of A*Y in a dense scratch row and then masking it (the plain
  * definition), and it runs Algorithm 3 literally, projecting after the
- * Jacobi step as the algorithm prints it.
+ * preconditioner step as the algorithm prints it.  The preconditioner is
+ * Jacobi (M_1) or the projected block symmetric Gauss-Seidel (M_2), the
+ * latter swept column block by column block through the transposed pattern
+ * of P with a binary search for every coupled entry.
  *
  * Notation (Sections 3.1-3.4): P is n x nc with fixed pattern; J_i is the
  * sorted column set of row i (m_i entries); B_i = B_c(J_i,:) is m_i x k;
@@ -290,6 +293,103 @@ int orc_diag_inverse(int n, const int *Ap, const int *Aj, const double *Av, doub
     return ORC_OK;
 }
 
+/* Position of entry (l, j) of P in the row-wise value arrays, -1 if row l
+ * does not hold column j (columns of a row are sorted). */
+static long find_entry(const int *Pp, const int *Pj, int l, int j)
+{
+    int lo = Pp[l], hi = Pp[l + 1];
+    while (lo < hi) {
+        int mid = lo + (hi - lo) / 2;
+        if (Pj[mid] < j) lo = mid + 1; else hi = mid;
+    }
+    return (lo < Pp[l + 1] && Pj[lo] == j) ? (long)lo : -1;
+}
+
+/* ------------------------------------------------------------------------
+ * Block symmetric Gauss-Seidel on K (Section 3.4, the M_SGS of the projected
+ * SGS preconditioner M_2): z = (L + D)^{-T} D (L + D)^{-1} r with
+ * K = L + D + L^T, p ordered row-wise.  K couples only entries of the same
+ * column of P, so its block for column j is A(I_j, I_j) (I_j = the rows of P
+ * holding column j), and in the row-wise order of p the rows of a block come
+ * in increasing row index: L of a block is the strictly lower part of
+ * A(I_j, I_j).  Each block is swept on its own:
+ *   forward   (L + D) u = r     (rows of I_j in increasing order),
+ *   diagonal  w = D u,
+ *   backward  (L + D)^T z = w   (rows in decreasing order; the entry
+ *             (L + D)^T(i, l) = K(l, i) = A(l, i) = A(i, l), A symmetric).
+ * ------------------------------------------------------------------------ */
+int orc_sgs_apply(int n, int nc, const int *Ap, const int *Aj, const double *Av,
+                  const int *Pp, const int *Pj, const double *r, double *z)
+{
+    long nnz = Pp[n];
+    /* the rows of every column of P, in increasing row order */
+    int *colp = (int *)calloc((size_t)nc + 2, sizeof(int));
+    int *crow = (int *)malloc(sizeof(int) * (size_t)(nnz + 1));
+    long *cpos = (long *)malloc(sizeof(long) * (size_t)(nnz + 1));
+    double *u = (double *)malloc(sizeof(double) * (size_t)(nnz + 1));
+    if (!colp || !crow || !cpos || !u) {
+        free(colp); free(crow); free(cpos); free(u);
+        return ORC_ERR_NOMEM;
+    }
+    for (long q = 0; q < nnz; ++q) colp[Pj[q] + 1]++;
+    for (int j = 0; j < nc; ++j) colp[j + 1] += colp[j];
+    for (int i = 0; i < n; ++i)
+        for (int q = Pp[i]; q < Pp[i + 1]; ++q) {
+            int t = colp[Pj[q]]++;
+            crow[t] = i;
+            cpos[t] = q;
+        }
+    for (int j = nc; j > 0; --j) colp[j] = colp[j - 1];
+    colp[0] = 0;
+    int status = ORC_OK;
+    for (int j = 0; j < nc && status == ORC_OK; ++j) {
+        for (int t = colp[j]; t < colp[j + 1]; ++t) {
+            int i = crow[t];
+            double acc = r[cpos[t]], d = 0;
+            for (int e = Ap[i]; e < Ap[i + 1]; ++e) {
+                int l = Aj[e];
+                if (l == i) {
+                    d = Av[e];
+                } else if (l < i) {
+                    long ql = find_entry(Pp, Pj, l, j);
+                    if (ql >= 0) acc -= Av[e] * u[ql];
+                }
+            }
+            if (!(d > 0)) { status = ORC_ERR_DIAG; break; }
+            u[cpos[t]] = acc / d;
+        }
+        for (int t = colp[j + 1] - 1; t >= colp[j] && status == ORC_OK; --t) {
+            int i = crow[t];
+            double d = 0;
+            for (int e = Ap[i]; e < Ap[i + 1]; ++e)
+                if (Aj[e] == i) d = Av[e];
+            double acc = d * u[cpos[t]];
+            for (int e = Ap[i]; e < Ap[i + 1]; ++e) {
+                int l = Aj[e];
+                if (l > i) {
+                    long ql = find_entry(Pp, Pj, l, j);
+                    if (ql >= 0) acc -= Av[e] * z[ql];
+                }
+            }
+            z[cpos[t]] = acc / d;
+        }
+    }
+    free(colp); free(crow); free(cpos); free(u);
+    return status;
+}
+
+/* M^{-1} r for the preconditioners of Section 3.4: Jacobi M_J = diag(K)
+ * (precond 0) or block SGS (precond 1). */
+static int apply_minv(int n, int nc, const int *Ap, const int *Aj, const double *Av,
+                      const int *Pp, const int *Pj, const double *dinv, int precond,
+                      const double *r, double *z)
+{
+    if (precond == 1) return orc_sgs_apply(n, nc, Ap, Aj, Av, Pp, Pj, r, z);
+    for (int i = 0; i < n; ++i)
+        for (int s = Pp[i]; s < Pp[i + 1]; ++s) z[s] = dinv[i] * r[s];
+    return ORC_OK;
+}
+
 double orc_dot(long nnz, const double *x, const double *y)
 {
     double s = 0;
@@ -298,8 +398,9 @@ double orc_dot(long nnz, const double *x, const double *y)
 }
 
 /* ------------------------------------------------------------------------
- * Algorithm 3 (EMIN_PCG) on Pi_B K Pi_B, Jacobi preconditioner, from the
- * residual r (overwritten) and the correction dw (accumulated, usually 0).
+ * Algorithm 3 (EMIN_PCG) on Pi_B K Pi_B from the residual r (overwritten)
+ * and the correction dw (accumulated, usually 0), with the Jacobi
+ * preconditioner (precond 0) or the projected block SGS (precond 1).
  *   z = Pi_B M^{-1} r;  gamma = r^T z;  y = z (first) or z + (gamma/gamma_old) y;
  *   y_ = Pi_B K y;  alpha = gamma / y^T y_;  dE_k = gamma alpha;
  *   stop if dE_k < tau dE_1 (step not applied);  dw += alpha y;  r -= alpha y_.
@@ -314,7 +415,8 @@ double orc_dot(long nnz, const double *x, const double *y)
 int orc_pcg(int n, int nc, int k, const int *Ap, const int *Aj, const double *Av,
             const int *Pp, const int *Pj, const double *Q, const double *dinv,
             double *r, double *dw, int maxit, double tau, double gamma_floor,
-            double *dE_hist, int *n_computed, int *n_applied, double *gamma_last)
+            double *dE_hist, int *n_computed, int *n_applied, double *gamma_last,
+            int precond)
 {
     long nnz = Pp[n];
     double *z = (double *)malloc(sizeof(double) * (size_t)(nnz + 1));
@@ -324,8 +426,8 @@ int orc_pcg(int n, int nc, int k, const int *Ap, const int *Aj, const double *Av
     double gamma_old = 0, dE1 = 0, gamma = 0;
     int status = ORC_OK, computed = 0, applied = 0;
     for (int it = 1; it <= maxit; ++it) {
-        for (int i = 0; i < n; ++i)
-            for (int s = Pp[i]; s < Pp[i + 1]; ++s) z[s] = dinv[i] * r[s];
+        status = apply_minv(n, nc, Ap, Aj, Av, Pp, Pj, dinv, precond, r, z);
+        if (status != ORC_OK) break;
         orc_project(n, k, Pp, Q, z);
         gamma = orc_dot(nnz, r, z);
         if (gamma <= gamma_floor) break;
@@ -379,7 +481,8 @@ int orc_minimize(int n, int nc, int k, const int *Ap, const int *Aj, const doubl
                  const int *Pp, const int *Pj, const double *B, const double *Bc,
                  double *P, double *P0_restored, double *Q, double *W, int *rank,
                  double tol, int pinv, int maxit, double tau,
-                 double *dE_hist, int *n_computed, int *n_applied, int *n_deficient)
+                 double *dE_hist, int *n_computed, int *n_applied, int *n_deficient,
+                 int precond)
 {
     long nnz = Pp[n];
     int st = orc_setup(n, nc, k, Pp, Pj, Bc, B, P, Q, W, rank, tol, pinv, n_deficient);
@@ -398,7 +501,7 @@ int orc_minimize(int n, int nc, int k, const int *Ap, const int *Aj, const doubl
         orc_project(n, k, Pp, Q, r);
         for (long q = 0; q < nnz; ++q) r[q] = -r[q];
         st = orc_pcg(n, nc, k, Ap, Aj, Av, Pp, Pj, Q, dinv, r, dw, maxit, tau,
-                     1e-28 * ref, dE_hist, n_computed, n_applied, NULL);
+                     1e-28 * ref, dE_hist, n_computed, n_applied, NULL, precond);
         for (long q = 0; q < nnz; ++q) P[q] += dw[q];
     }
     free(dinv); free(r); free(dw);
@@ -460,7 +563,7 @@ void orc_lsq(int n, int k, const int *Pp, const double *Q, const double *W,
 int orc_backward(int n, int nc, int k, const int *Ap, const int *Aj, const double *Av,
                  const int *Pp, const int *Pj, const double *Q, const double *W,
                  const double *P, const double *dLdP, int maxit, double tau,
-                 double *U, double *dLdA, double *dLdB, int *n_applied)
+                 double *U, double *dLdA, double *dLdB, int *n_applied, int precond)
 {
     long nnz = Pp[n];
     double *dinv = (double *)malloc(sizeof(double) * (size_t)(n + 1));
@@ -477,7 +580,7 @@ int orc_backward(int n, int nc, int k, const int *Ap, const int *Aj, const doubl
             for (int s = Pp[i]; s < Pp[i + 1]; ++s) ref += r[s] * dinv[i] * r[s];
         orc_project(n, k, Pp, Q, r);
         st = orc_pcg(n, nc, k, Ap, Aj, Av, Pp, Pj, Q, dinv, r, U, maxit, tau,
-                     1e-28 * ref, hist, &computed, &applied, NULL);
+                     1e-28 * ref, hist, &computed, &applied, NULL, precond);
     }
     if (st == ORC_OK) {
         orc_kprod(n, nc, Ap, Aj, Av, Pp, Pj, U, S);

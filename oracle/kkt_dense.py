@@ -12,7 +12,9 @@ densely with NumPy so that it can be compared with the sparse oracle:
                    ``numpy.linalg.solve`` (``lstsq`` if singular).
 * ``nullspace_pcg`` the null-space method the paper calls equivalent to the
                    restricted PCG (after Eq. (projSys)): CG on Z^T K Z with
-                   preconditioner Z^T D_K^{-1} Z, Z from a full QR of C^T.
+                   preconditioner Z^T D_K^{-1} Z (or Z^T M_SGS^{-1} Z), Z from
+                   a full QR of C^T.
+* ``sgs_inverse``  (L + D)^{-T} D (L + D)^{-1} of K by dense triangular solves.
 """
 from __future__ import annotations
 
@@ -70,15 +72,28 @@ def nullspace_basis(prob):
     return Qf[:, rank:], Qf[:, :rank]
 
 
-def nullspace_pcg(prob, p0, maxit):
-    """Preconditioned CG on Z^T K Z x = -Z^T K p0 with M^{-1} = Z^T D_K^{-1} Z,
-    from x = 0.  Returns the iterates p0 + Z x_k (k = 0..maxit) and the
-    energy decrements gamma_k alpha_k."""
+def sgs_inverse(K):
+    """M_SGS^{-1} = (L + D)^{-T} D (L + D)^{-1} of K = L + D + L^T (Section 3.4),
+    as a dense matrix, for p in K's own (row-wise) order."""
+    LD = np.tril(K)
+    D = np.diag(np.diag(K))
+    Linv = np.linalg.solve(LD, np.eye(K.shape[0]))
+    return Linv.T @ D @ Linv
+
+
+def nullspace_pcg(prob, p0, maxit, precond="jacobi"):
+    """Preconditioned CG on Z^T K Z x = -Z^T K p0 from x = 0, with the
+    reduced preconditioner M^{-1} = Z^T D_K^{-1} Z (Jacobi, M_1) or
+    Z^T M_SGS^{-1} Z (projected SGS, M_2).  Returns the iterates
+    p0 + Z x_k (k = 0..maxit) and the energy decrements gamma_k alpha_k."""
     K = dense_K(prob)
     Z, _ = nullspace_basis(prob)
     d = np.diag(K)
     H = Z.T @ K @ Z
-    Minv = Z.T @ (Z / d[:, None])
+    if precond == "sgs":
+        Minv = Z.T @ sgs_inverse(K) @ Z
+    else:
+        Minv = Z.T @ (Z / d[:, None])
     x = np.zeros(Z.shape[1])
     r = -Z.T @ (K @ p0)
     iters, dE = [p0.copy()], []

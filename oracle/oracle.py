@@ -61,6 +61,7 @@ def lib():
             L.orc_backward.restype = ctypes.c_int
             L.orc_outer.restype = ctypes.c_int
             L.orc_diag_inverse.restype = ctypes.c_int
+            L.orc_sgs_apply.restype = ctypes.c_int
             L.orc_dot.restype = ctypes.c_double
             _lib = L
     return _lib
@@ -91,7 +92,12 @@ class OracleError(RuntimeError):
 class Oracle:
     """Plain FP64 oracle bound to one problem (A, pattern of P, B, B_c)."""
 
-    def __init__(self, prob, pinv: bool = False, tol: float = RANK_TOL):
+    PRECONDS = {"jacobi": 0, "sgs": 1}
+
+    def __init__(self, prob, pinv: bool = False, tol: float = RANK_TOL, precond: str = "jacobi"):
+        """precond: "jacobi" (M_1 of Section 3.4) or "sgs" (the projected
+        block symmetric Gauss-Seidel M_2)."""
+        self.precond = self.PRECONDS[precond]
         self.n, self.nc, self.k = prob.n, prob.nc, prob.k
         self.Ap, self.Aj, self.Av = _i32(prob.A_rowptr), _i32(prob.A_col), _f64(prob.A_val)
         self.Pp, self.Pj = _i32(prob.P_rowptr), _i32(prob.P_col)
@@ -130,6 +136,15 @@ class Oracle:
         lib().orc_kprod(self.n, self.nc, _ip(self.Ap), _ip(self.Aj), _dp(self.Av),
                         _ip(self.Pp), _ip(self.Pj), _dp(Y), _dp(out))
         return out
+
+    def sgs(self, r):
+        """(L + D)^{-T} D (L + D)^{-1} r, K = L + D + L^T block by block."""
+        z = np.zeros(self.nnz_p)
+        st = lib().orc_sgs_apply(self.n, self.nc, _ip(self.Ap), _ip(self.Aj), _dp(self.Av),
+                                 _ip(self.Pp), _ip(self.Pj), _dp(_f64(r)), _dp(z))
+        if st != 0:
+            raise OracleError(st, "sgs")
+        return z
 
     def project(self, x):
         x = _f64(x).copy()
@@ -175,7 +190,8 @@ class Oracle:
                            _ip(self.Pp), _ip(self.Pj), _dp(self.Q), _dp(self.dinv),
                            _dp(r), _dp(dw), int(maxit), ctypes.c_double(tau),
                            ctypes.c_double(gamma_floor), _dp(hist),
-                           ctypes.byref(nc_), ctypes.byref(na_), ctypes.byref(g))
+                           ctypes.byref(nc_), ctypes.byref(na_), ctypes.byref(g),
+                           int(self.precond))
         return dw, hist[:nc_.value].copy(), na_.value, st
 
     def minimize(self, maxit, tau=0.0):
@@ -195,7 +211,7 @@ class Oracle:
                                 _dp(self.Av), _ip(self.Pp), _ip(self.Pj), _dp(self.Q),
                                 _dp(self.W), _dp(_f64(P)), _dp(_f64(dLdP)), int(maxit),
                                 ctypes.c_double(tau), _dp(U), _dp(dA), _dp(dB),
-                                ctypes.byref(na_))
+                                ctypes.byref(na_), int(self.precond))
         if st != 0:
             raise OracleError(st, "backward")
         return dA, dB, U, na_.value
