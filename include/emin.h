@@ -60,12 +60,21 @@ enum { EMIN_FP64 = 0,   /* every step in IEEE double                           *
                         /* factorisation, trace/step reductions and the final  */
                         /* constraint-restoring projection in double           */
 };
-enum { EMIN_JACOBI = 0 };                       /* M_1 of Section 3.4          */
+/* Preconditioners of Section 3.4.  EMIN_JACOBI: M_1, the Jacobi scaling of
+ * Pi_B K Pi_B (Theorem 1).  EMIN_SGS: M_2 = Z^T M_SGS^{-1} Z, the projected
+ * block symmetric Gauss-Seidel, M_SGS^{-1} = (L + D)^{-T} D (L + D)^{-1} with
+ * K = L + D + L^T in the row-wise order of p (per column block of P, rows in
+ * increasing order), applied as z = Pi_B M_SGS^{-1} r.  EMIN_SGS builds a
+ * plan on the host at create (copies of both patterns; time and memory grow
+ * with the products inside the column blocks) and fails with EMIN_ERR_ARG
+ * when one column of P has more than 65,535 rows or a group of columns with
+ * the same rows needs more than 200 KB of shared memory. */
+enum { EMIN_JACOBI = 0, EMIN_SGS = 1 };
 enum { EMIN_RANK_STRICT = 0, EMIN_RANK_PINV = 1 };
 
 typedef struct {
     int precision;    /* EMIN_FP64 or EMIN_MIXED                               */
-    int precond;      /* EMIN_JACOBI                                           */
+    int precond;      /* EMIN_JACOBI or EMIN_SGS                               */
     int rank_policy;  /* EMIN_RANK_STRICT: a rank-deficient row is an error;   */
                       /* EMIN_RANK_PINV: pseudo-inverse of that row's Gram     */
                       /* matrix (the SVD branch of Algorithm 2), counted in    */

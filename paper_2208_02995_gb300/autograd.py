@@ -26,7 +26,7 @@ class EminProblem:
     A's CSR pattern, P's pattern, the tentative P0, B_c, and a default B."""
 
     def __init__(self, n, nc, k, A_rowptr, A_col, P_rowptr, P_col, P0_val, B, Bc,
-                 precision="fp64", device="cuda"):
+                 precision="fp64", device="cuda", precond="jacobi"):
         def t(x, dt):
             return torch.as_tensor(x).to(device=device, dtype=dt).contiguous()
         self.n, self.nc, self.k = int(n), int(nc), int(k)
@@ -36,11 +36,12 @@ class EminProblem:
         self.B = t(B, torch.float64).reshape(self.n, self.k)
         self.Bc = t(Bc, torch.float64).reshape(self.nc, self.k)
         self.precision = precision
+        self.precond = precond
 
     @classmethod
-    def from_problem(cls, prob, precision="fp64", device="cuda"):
+    def from_problem(cls, prob, precision="fp64", device="cuda", precond="jacobi"):
         return cls(prob.n, prob.nc, prob.k, prob.A_rowptr, prob.A_col, prob.P_rowptr,
-                   prob.P_col, prob.P0_val, prob.B, prob.Bc, precision, device)
+                   prob.P_col, prob.P0_val, prob.B, prob.Bc, precision, device, precond)
 
     def context(self, A_val, B=None, precision=None):
         """A library context holding these values (stream: the current one)."""
@@ -50,7 +51,7 @@ class EminProblem:
                   self.P_rowptr, self.P_col, self.P0,
                   B.detach().contiguous().double().reshape(self.n, self.k), self.Bc]
         return Context(n=self.n, nc=self.nc, k=self.k, arrays=arrays,
-                       precision=precision, on_device=True)
+                       precision=precision, on_device=True, precond=self.precond)
 
 
 class EminSolve(torch.autograd.Function):

@@ -51,6 +51,16 @@ struct emin_ctx {
     unsigned int *bmap = nullptr;
     int *tile_map = nullptr;
     int ntiles = 0;
+    // projected block SGS plan (EMIN_SGS), built once per context
+    int sgs_ngroups = 0, sgs_cap = 0, sgs_gmax = 0;
+    long long sgs_nrows = 0, sgs_nf = 0, sgs_nb = 0;
+    int *sgs_hdr = nullptr, *sgs_rpos = nullptr, *sgs_flvl = nullptr, *sgs_blvl = nullptr;
+    int *sgs_foptr = nullptr, *sgs_boptr = nullptr, *sgs_fa = nullptr, *sgs_ba = nullptr;
+    int *sgs_fgrow = nullptr, *sgs_bgrow = nullptr;
+    unsigned short *sgs_frow = nullptr, *sgs_brow = nullptr, *sgs_fidx = nullptr,
+                   *sgs_bidx = nullptr;
+    float *sgs_fval32 = nullptr, *sgs_bval32 = nullptr;
+    double *sgs_fval64 = nullptr, *sgs_bval64 = nullptr;
     double *Pstar = nullptr, *t64c = nullptr;
     // restricted PCG workspaces
     Work<double> w64;   // forward, EMIN_FP64
@@ -170,17 +180,45 @@ Ops<double> plain_ops64(const emin_ctx *c) {
                        c->maxrow_p, c->lanes};
 }
 
+// the SGS plan with the values of one precision (an empty plan: Jacobi)
+template <class T>
+SgsOps<T> sgs_ops(const emin_ctx *c, const T *fval, const T *bval) {
+    SgsOps<T> s;
+    if (c->opts.precond != EMIN_SGS || c->sgs_ngroups <= 0) return s;
+    s.ngroups = c->sgs_ngroups;
+    s.nrows = c->sgs_nrows;
+    s.cap = c->sgs_cap;
+    s.gmax = c->sgs_gmax;
+    s.hdr = c->sgs_hdr;
+    s.rpos = c->sgs_rpos;
+    s.flvl = c->sgs_flvl;
+    s.foptr = c->sgs_foptr;
+    s.blvl = c->sgs_blvl;
+    s.boptr = c->sgs_boptr;
+    s.frow = c->sgs_frow;
+    s.fidx = c->sgs_fidx;
+    s.brow = c->sgs_brow;
+    s.bidx = c->sgs_bidx;
+    s.fval = fval;
+    s.bval = bval;
+    return s;
+}
+
 // the iteration's operator A^ with its plan
 Ops<double> iter_ops64(const emin_ctx *c) {
-    return Ops<double>{c->n, c->nc, c->k, c->Ap, c->Aj, c->Ah64, c->Pp, c->Pj, c->Bc, c->Ginv,
+    Ops<double> o{c->n, c->nc, c->k, c->Ap, c->Aj, c->Ah64, c->Pp, c->Pj, c->Bc, c->Ginv,
                        c->qv64, c->sell_ptr, c->sa64, c->soff, c->smap, c->sw, nullptr, c->boff, c->blen, c->bmap, c->tile_map, c->ntiles,
                        c->maxrow_p, c->lanes};
+    o.sgs = sgs_ops<double>(c, c->sgs_fval64, c->sgs_bval64);
+    return o;
 }
 
 Ops<float> iter_ops32(const emin_ctx *c) {
-    return Ops<float>{c->n, c->nc, c->k, c->Ap, c->Aj, c->Ah32, c->Pp, c->Pj, c->Bc32, c->Ginv32,
+    Ops<float> o{c->n, c->nc, c->k, c->Ap, c->Aj, c->Ah32, c->Pp, c->Pj, c->Bc32, c->Ginv32,
                       c->qv32, c->sell_ptr, c->sa32, c->soff, c->smap, c->sw, c->spk32, c->boff, c->blen, c->bmap, c->tile_map, c->ntiles,
                       c->maxrow_p, c->lanes};
+    o.sgs = sgs_ops<float>(c, c->sgs_fval32, c->sgs_bval32);
+    return o;
 }
 
 template <class T>
@@ -190,6 +228,7 @@ int alloc_work(emin_ctx *c, Work<T> &w, bool vectors) {
         EMIN_TRY(dalloc(c, &w.Y, c->nnz_p));
         EMIN_TRY(dalloc(c, &w.Yb, c->nnz_p));
         EMIN_TRY(dalloc(c, &w.X, c->nnz_p));
+        if (c->opts.precond == EMIN_SGS) EMIN_TRY(dalloc(c, &w.Z, c->nnz_p));
     }
     EMIN_TRY(dalloc(c, &w.st, 1));
     EMIN_TRY(dalloc(c, &w.partials, kMaxGrid));
@@ -213,8 +252,90 @@ int start_pcg(emin_ctx *c, const Ops<T> &o, Work<T> &w, const T *x0) {
     if (x0) launch_kprod<T>(c->L, o, x0, w.R, 0, DOT_NONE, w, 0);
     launch_update<T>(c->L, c->nnz_p, w, UPD_FLOOR);
     launch_project<T>(c->L, o, w.R, x0 ? T(-1) : T(1));
-    launch_update<T>(c->L, c->nnz_p, w, UPD_INIT);
+    if (o.sgs.ngroups > 0) {
+        // z~_0 = Pi (L^ + I)^{-T} (L^ + I)^{-1} r~_0, gamma_0 = <r~, z~>
+        launch_sgs_sweep<T>(c->L, o.sgs, w.R, w.Z, w.st);
+        launch_project<T>(c->L, o, w.Z, T(1));
+        launch_update<T>(c->L, c->nnz_p, w, UPD_GZ_INIT);
+    } else {
+        launch_update<T>(c->L, c->nnz_p, w, UPD_INIT);
+    }
     return check_launch();
+}
+
+template <class T>
+int upload(emin_ctx *c, T **dst, const std::vector<T> &src) {
+    EMIN_TRY(dalloc(c, dst, (long long)src.size()));
+    if (!src.empty())
+        EMIN_TRY(cuda_status(cudaMemcpyAsync(*dst, src.data(), sizeof(T) * src.size(),
+                                             cudaMemcpyHostToDevice, c->stream)));
+    return EMIN_OK;
+}
+
+// The projected block SGS plan from host copies of both patterns (the plan
+// builder is host code, run once per context), uploaded to the device.
+int build_sgs(emin_ctx *c) {
+    const int n = c->n;
+    std::vector<int> Ap(n + 1), Aj(c->nnz_a), Pp(n + 1), Pj(c->nnz_p);
+    EMIN_TRY(cuda_status(cudaMemcpyAsync(Ap.data(), c->Ap, sizeof(int) * (n + 1),
+                                         cudaMemcpyDeviceToHost, c->stream)));
+    EMIN_TRY(cuda_status(cudaMemcpyAsync(Aj.data(), c->Aj, sizeof(int) * c->nnz_a,
+                                         cudaMemcpyDeviceToHost, c->stream)));
+    EMIN_TRY(cuda_status(cudaMemcpyAsync(Pp.data(), c->Pp, sizeof(int) * (n + 1),
+                                         cudaMemcpyDeviceToHost, c->stream)));
+    EMIN_TRY(cuda_status(cudaMemcpyAsync(Pj.data(), c->Pj, sizeof(int) * c->nnz_p,
+                                         cudaMemcpyDeviceToHost, c->stream)));
+    EMIN_TRY(sync(c));
+    SgsHost h;
+    const int st = build_sgs_plan(n, c->nc, Ap.data(), Aj.data(), Pp.data(), Pj.data(), h);
+    if (st != EMIN_OK) {
+        std::snprintf(g_last_error, sizeof(g_last_error),
+                      "SGS plan: a column of P has more than 65535 rows or an invalid index");
+        return st;
+    }
+    // one group's block must fit the shared memory of one block of one warp
+    if ((long long)h.cap * (long long)sizeof(double) > 200LL * 1024) {
+        std::snprintf(g_last_error, sizeof(g_last_error),
+                      "SGS plan: a column group of %d values exceeds shared memory", h.cap);
+        return EMIN_ERR_ARG;
+    }
+    c->sgs_ngroups = h.ngroups;
+    c->sgs_cap = h.cap;
+    c->sgs_gmax = h.gmax;
+    c->sgs_nrows = (long long)h.rpos.size();
+    EMIN_TRY(upload(c, &c->sgs_hdr, h.hdr));
+    EMIN_TRY(upload(c, &c->sgs_rpos, h.rpos));
+    EMIN_TRY(upload(c, &c->sgs_flvl, h.flvl));
+    EMIN_TRY(upload(c, &c->sgs_blvl, h.blvl));
+    EMIN_TRY(upload(c, &c->sgs_foptr, h.foptr));
+    EMIN_TRY(upload(c, &c->sgs_boptr, h.boptr));
+    EMIN_TRY(upload(c, &c->sgs_fa, h.fa));
+    EMIN_TRY(upload(c, &c->sgs_ba, h.ba));
+    EMIN_TRY(upload(c, &c->sgs_fgrow, h.fgrow));
+    EMIN_TRY(upload(c, &c->sgs_bgrow, h.bgrow));
+    EMIN_TRY(upload(c, &c->sgs_frow, h.frow));
+    EMIN_TRY(upload(c, &c->sgs_brow, h.brow));
+    EMIN_TRY(upload(c, &c->sgs_fidx, h.fidx));
+    EMIN_TRY(upload(c, &c->sgs_bidx, h.bidx));
+    const long long nf = (long long)h.fidx.size(), nb = (long long)h.bidx.size();
+    if (c->opts.precision == EMIN_MIXED) {
+        EMIN_TRY(dalloc(c, &c->sgs_fval32, nf));
+        EMIN_TRY(dalloc(c, &c->sgs_bval32, nb));
+    } else {
+        EMIN_TRY(dalloc(c, &c->sgs_fval64, nf));
+        EMIN_TRY(dalloc(c, &c->sgs_bval64, nb));
+    }
+    c->sgs_nf = nf;
+    c->sgs_nb = nb;
+    return sync(c);  // the host vectors must outlive the transfers
+}
+
+// the SGS values A^ at the plan's couplings, in the precision of T
+template <class T>
+void form_sgs_values(emin_ctx *c, T *fval, T *bval) {
+    if (c->opts.precond != EMIN_SGS || c->sgs_ngroups <= 0) return;
+    launch_sgs_values<T>(c->L, sgs_ops<T>(c, fval, bval), c->sgs_fgrow, c->sgs_bgrow, c->sgs_fa,
+                         c->sgs_ba, c->Aj, c->Av, c->dsq, fval, bval);
 }
 
 // A^ and q in double (the FP64 path, or the adjoint of a mixed context)
@@ -224,6 +345,7 @@ void form_scaled64(emin_ctx *c) {
     else
         launch_scale_a<double>(c->L, c->n, c->Ap, c->Aj, c->Av, c->dsq, c->Ah64);
     if (c->k == 1) launch_qvec_k1<double>(c->L, c->n, c->Pp, c->Pj, c->Bc, c->qv64);
+    if (c->sgs_fval64) form_sgs_values<double>(c, c->sgs_fval64, c->sgs_bval64);
     c->have64 = true;
 }
 
@@ -241,12 +363,14 @@ int run_setup(emin_ctx *c) {
             launch_to_float(L, c->Bc, c->Bc32, (long long)c->nc * c->k);
             launch_sell_values<float>(L, c->n, c->Ap, c->Aj, c->Av, c->dsq, c->sell_ptr, c->sa32,
                                       c->sw, c->spk32);
+            form_sgs_values<float>(c, c->sgs_fval32, c->sgs_bval32);
             EMIN_TRY(start_pcg<float>(c, iter_ops32(c), c->w32, c->t32a));
         } else {
             launch_setup_k1<double>(L, c->n, c->dpos, c->Av, c->Pp, c->Pj, c->Bc, c->B, c->P0_in,
                                     c->opts.rank_policy, c->dint, c->dint + 2, c->dsq, c->dhalf,
                                     c->Ginv, c->qv64, c->P0, c->t64c);
             launch_sell_values<double>(L, c->n, c->Ap, c->Aj, c->Av, c->dsq, c->sell_ptr, c->sa64);
+            form_sgs_values<double>(c, c->sgs_fval64, c->sgs_bval64);
             c->have64 = true;
             EMIN_TRY(start_pcg<double>(c, iter_ops64(c), c->w64, c->t64c));
         }
@@ -268,6 +392,7 @@ int run_setup(emin_ctx *c) {
         else
             launch_scale_a<float>(L, c->n, c->Ap, c->Aj, c->Av, c->dsq, c->Ah32);
         if (c->k == 1) launch_qvec_k1<float>(L, c->n, c->Pp, c->Pj, c->Bc, c->qv32);
+        form_sgs_values<float>(c, c->sgs_fval32, c->sgs_bval32);
         launch_row_scale<double, float>(L, c->n, c->Pp, c->lanes, c->dhalf, 1.0, c->P0, c->t32a);
         EMIN_TRY(start_pcg<float>(c, iter_ops32(c), c->w32, c->t32a));
     } else {
@@ -505,6 +630,8 @@ int create_impl(emin_ctx *c, const int *A_rowptr, const int *A_col, const double
         }
     }
 
+    if (c->opts.precond == EMIN_SGS && n > 0) EMIN_TRY(build_sgs(c));
+
     EMIN_TRY(run_setup(c));
     return read_flags(c);
 }
@@ -523,7 +650,15 @@ int launch_iterations(emin_ctx *c, const Ops<T> &o, Work<T> &w, int n_iters, boo
         if (t) cudaEventRecordWithFlags(c->events[(size_t)it * 2], c->stream, cudaEventRecordExternal);
         launch_kprod<T>(c->L, o, w.Y, w.Yb, 1, DOT_ALPHA, w, 1);
         if (t) cudaEventRecordWithFlags(c->events[(size_t)it * 2 + 1], c->stream, cudaEventRecordExternal);
-        launch_update<T>(c->L, c->nnz_p, w, UPD_STEP);
+        if (o.sgs.ngroups > 0) {
+            // projected SGS: the step, then z~ = Pi M^-1 r~ and gamma = <r~, z~>
+            launch_update<T>(c->L, c->nnz_p, w, UPD_XR);
+            launch_sgs_sweep<T>(c->L, o.sgs, w.R, w.Z, w.st);
+            launch_project<T>(c->L, o, w.Z, T(1));
+            launch_update<T>(c->L, c->nnz_p, w, UPD_GZ_STEP);
+        } else {
+            launch_update<T>(c->L, c->nnz_p, w, UPD_STEP);
+        }
     }
     return check_launch();
 }
@@ -566,6 +701,7 @@ void build_while_graph(emin_ctx *c, const Ops<T> &o, Work<T> &w) {
             cudaGraph_t captured = nullptr;
             ok = cudaStreamEndCapture(c->stream, &captured) == cudaSuccess;
         }
+        w.gwhile_per_pass = (int)(launches_so_far() - before);
         note_launches(before - launches_so_far());  // captured, not run
     }
     if (ok && cudaGraphInstantiate(&w.gwhile, graph, 0) != cudaSuccess) w.gwhile = nullptr;
@@ -611,12 +747,13 @@ int iterate_impl(emin_ctx *c, const Ops<T> &o, Work<T> &w, int n_iters, double t
                 }
             }
             cudaGetLastError();
+            w.gexec_launches = launches_so_far() - before;
             note_launches(before - launches_so_far());  // captured, not run
             w.gn = n_iters;
             w.gtimed = tkey;
         }
         if (w.gexec && cudaGraphLaunch(w.gexec, c->stream) == cudaSuccess) {
-            note_launches(3LL * n_iters);
+            note_launches(w.gexec_launches);
             launched = true;
         }
         cudaGetLastError();
@@ -624,7 +761,7 @@ int iterate_impl(emin_ctx *c, const Ops<T> &o, Work<T> &w, int n_iters, double t
     if (!launched) EMIN_TRY(launch_iterations<T>(c, o, w, n_iters, timed));
     EMIN_TRY(check_launch());
     EMIN_TRY(read_state(c, w.st));
-    if (looped) note_launches(4LL * (n_iters - c->hstate->loop_left));  // passes x 4 kernels
+    if (looped) note_launches((long long)w.gwhile_per_pass * (n_iters - c->hstate->loop_left));
     if (timed) {
         for (int it = 0; it < n_iters; it += c->timing) {
             float ms = 0.f;
@@ -698,7 +835,8 @@ int emin_create(emin_ctx **out, int n, int nc, int k, const int *A_rowptr, const
     emin_opts o;
     emin_default_opts(&o);
     if (opts) o = *opts;
-    if ((o.precision != EMIN_FP64 && o.precision != EMIN_MIXED) || o.precond != EMIN_JACOBI ||
+    if ((o.precision != EMIN_FP64 && o.precision != EMIN_MIXED) ||
+        (o.precond != EMIN_JACOBI && o.precond != EMIN_SGS) ||
         (o.rank_policy != EMIN_RANK_STRICT && o.rank_policy != EMIN_RANK_PINV))
         return EMIN_ERR_ARG;
     emin_ctx *c = new (std::nothrow) emin_ctx();
@@ -862,6 +1000,11 @@ int emin_backward(emin_ctx *c, const double *dL_dP, double *dL_dAval, double *dL
         if (!c->Ah64) EMIN_TRY(dalloc(c, &c->Ah64, c->nnz_a));
         if (c->sell_ptr && !c->sa64) EMIN_TRY(dalloc(c, &c->sa64, c->nnz_sell));
         if (c->k == 1 && !c->qv64) EMIN_TRY(dalloc(c, &c->qv64, c->nnz_p));
+        if (c->sgs_ngroups > 0 && !c->sgs_fval64) {
+            EMIN_TRY(dalloc(c, &c->sgs_fval64, c->sgs_nf));
+            EMIN_TRY(dalloc(c, &c->sgs_bval64, c->sgs_nb));
+            c->have64 = false;
+        }
     }
     if (!c->have64) form_scaled64(c);
     const Ops<double> o = iter_ops64(c);

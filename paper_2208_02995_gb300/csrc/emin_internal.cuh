@@ -12,6 +12,8 @@
 #pragma once
 #include <cuda_runtime.h>
 
+#include <vector>
+
 #include <cstddef>
 #include <cstdint>
 
@@ -59,13 +61,20 @@ struct DevState {
 
 // reduction targets of the masked-product kernel
 enum DotMode : int { DOT_NONE = 0, DOT_ALPHA = 1, DOT_AUX = 2 };
-// modes of the update kernel
-enum UpdMode : int { UPD_INIT = 0, UPD_STEP = 1, UPD_FLOOR = 2 };
+// modes of the update kernel: UPD_STEP applies the step and forms gamma =
+// <r~, r~> (Jacobi: z = r); UPD_INIT forms gamma_0; UPD_FLOOR sets the
+// convergence floor from the residual; with another preconditioner the step
+// (UPD_XR, no reduction) and gamma = <r~, z~> (UPD_GZ_INIT / UPD_GZ_STEP,
+// after z is formed) are separate passes
+enum UpdMode : int {
+    UPD_INIT = 0, UPD_STEP = 1, UPD_FLOOR = 2, UPD_XR = 3, UPD_GZ_INIT = 4, UPD_GZ_STEP = 5
+};
 
 // One restricted PCG workspace in value type T.
 template <class T>
 struct Work {
     T *R = nullptr, *Y = nullptr, *Yb = nullptr, *X = nullptr;
+    T *Z = nullptr;  // preconditioned residual (SGS only; Jacobi uses z = r)
     DevState *st = nullptr;
     double *partials = nullptr;
     double *hist = nullptr;
@@ -73,9 +82,28 @@ struct Work {
     // the captured iteration loop (CUDA graph) for gn iterations
     cudaGraphExec_t gexec = nullptr;
     int gn = -1, gtimed = -1;
+    long long gexec_launches = 0;  // kernels in the unrolled graph
     // one iteration as the body of a conditional while node: runs until the
     // call's count is used up or the stop test fires, for any count
     cudaGraphExec_t gwhile = nullptr;
+    int gwhile_per_pass = 0;  // kernels in one pass of the while body
+};
+
+// The projected block SGS plan on the device (see sgs.cu): per group a
+// header of 8 ints (rows m, columns G, first plan row r0, forward levels
+// start / count, backward levels start / count, first column); per plan row
+// the position of its first entry; per sweep the rows in level order (local
+// index), the level boundaries, each row's couplings (local index, A^ value).
+template <class T>
+struct SgsOps {
+    int ngroups = 0;
+    long long nrows = 0;  // plan rows (sum of the groups' rows)
+    int cap = 0;          // largest m * G (shared memory per warp, in values)
+    int gmax = 0;         // largest G
+    const int *hdr = nullptr, *rpos = nullptr;
+    const int *flvl = nullptr, *foptr = nullptr, *blvl = nullptr, *boptr = nullptr;
+    const unsigned short *frow = nullptr, *fidx = nullptr, *brow = nullptr, *bidx = nullptr;
+    const T *fval = nullptr, *bval = nullptr;
 };
 
 // Everything a masked-product launch needs to know about the problem.
@@ -114,6 +142,7 @@ struct Ops {
     int ntiles;
     int maxrow;                   // longest row of P
     int lanes;                    // lanes per row of the row kernels (1 or 32)
+    SgsOps<T> sgs;                // projected block SGS (ngroups 0: Jacobi)
 };
 
 struct Launch {
@@ -206,6 +235,21 @@ void launch_state_reset(const Launch &L, DevState *st);
 void set_iter_attributes();
 int staged_blocks_per_sm();
 int pk_blocks_per_sm(int double_precision);
+
+// projected block SGS (sgs.cu)
+struct SgsHost {
+    int ngroups = 0, cap = 0, gmax = 0;
+    std::vector<int> hdr, rpos, flvl, blvl, foptr, boptr, fa, ba, fgrow, bgrow;
+    std::vector<unsigned short> frow, brow, fidx, bidx;
+};
+int build_sgs_plan(int n, int nc, const int *Ap, const int *Aj, const int *Pp, const int *Pj,
+                   SgsHost &out);
+template <class T>
+void launch_sgs_values(const Launch &L, const SgsOps<T> &s, const int *fgrow, const int *bgrow,
+                       const int *fa, const int *ba, const int *Aj, const double *Av,
+                       const double *dsq, T *fval, T *bval);
+template <class T>
+void launch_sgs_sweep(const Launch &L, const SgsOps<T> &s, const T *R, T *Z, const DevState *st);
 void set_adjoint_attributes();
 void launch_state_begin(const Launch &L, DevState *st, double tau, int n_iters);
 // the while-loop control of the captured iteration graph (one thread)

@@ -669,7 +669,7 @@ __device__ __forceinline__ double2 axpy4(double b, double2 y, double2 r) {
     return make_double2(fma(b, y.x, r.x), fma(b, y.y, r.y));
 }
 
-// y~ = r~ + beta y~
+// y~ = z~ + beta y~ (z~ = r~ for Jacobi; R is z~)
 template <class T>
 __global__ void __launch_bounds__(kBlock)
 k_ydir_flat(long long count, const T *__restrict__ R, T *__restrict__ Y, const DevState *st) {
@@ -688,22 +688,21 @@ k_ydir_flat(long long count, const T *__restrict__ R, T *__restrict__ Y, const D
         Y[q] = fmat(beta, Y[q], R[q]);
 }
 
-// dW~ += alpha y~, r~ -= alpha y_~ (UPD_STEP), then gamma = <r~, r~>;
-// UPD_INIT only forms gamma; UPD_FLOOR sets the convergence floor.
+// dW~ += alpha y~, r~ -= alpha y_~ (UPD_STEP, UPD_XR), then gamma = <r~, r~>
+// (UPD_STEP, UPD_INIT) or <r~, z~> (UPD_GZ_*, Z given); UPD_FLOOR sets the
+// convergence floor from <r~, r~>.
 template <class T>
 __device__ __forceinline__ void upd1(T &r, T &x, T y, T yb, T alpha, int mode, Dot<T> &dot) {
-    if (mode == UPD_STEP) {
-        x = fmat(alpha, y, x);
-        r = fmat(-alpha, yb, r);
-    }
-    dot.add(r, r);
+    x = fmat(alpha, y, x);
+    r = fmat(-alpha, yb, r);
+    if (mode == UPD_STEP) dot.add(r, r);
 }
 
 template <class T>
 __global__ void __launch_bounds__(kBlock)
 k_update_flat(long long count, T *__restrict__ R, const T *__restrict__ Y,
               const T *__restrict__ Yb, T *__restrict__ X, DevState *st, double *partials,
-              int mode) {
+              int mode, const T *__restrict__ Z) {
     if (mode != UPD_FLOOR && st->stop) return;
     const T alpha = (T)st->alpha;
     using V = typename Vec<T>::V;
@@ -711,10 +710,19 @@ k_update_flat(long long count, T *__restrict__ R, const T *__restrict__ Y,
     const long long nv = count / W;
     const long long stride = (long long)gridDim.x * blockDim.x;
     Dot<T> dot;
-    const bool step = (mode == UPD_STEP);
+    const bool step = (mode == UPD_STEP || mode == UPD_XR);
+    const bool gz = (mode == UPD_GZ_INIT || mode == UPD_GZ_STEP);
     for (long long v = blockIdx.x * (long long)blockDim.x + threadIdx.x; v < nv; v += stride) {
         V r = reinterpret_cast<V *>(R)[v];
-        if (step) {
+        if (gz) {
+            const V z = reinterpret_cast<const V *>(Z)[v];
+            dot.add(r.x, z.x);
+            dot.add(r.y, z.y);
+            if constexpr (W == 4) {
+                dot.add(r.z, z.z);
+                dot.add(r.w, z.w);
+            }
+        } else if (step) {
             V x = reinterpret_cast<V *>(X)[v];
             const V y = reinterpret_cast<const V *>(Y)[v];
             const V yb = reinterpret_cast<const V *>(Yb)[v];
@@ -738,7 +746,9 @@ k_update_flat(long long count, T *__restrict__ R, const T *__restrict__ Y,
     for (long long q = nv * W + blockIdx.x * (long long)blockDim.x + threadIdx.x; q < count;
          q += stride) {
         T r = R[q];
-        if (step) {
+        if (gz) {
+            dot.add(r, Z[q]);
+        } else if (step) {
             T x = X[q];
             upd1(r, x, Y[q], Yb[q], alpha, mode, dot);
             X[q] = x;
@@ -747,11 +757,14 @@ k_update_flat(long long count, T *__restrict__ R, const T *__restrict__ Y,
             dot.add(r, r);
         }
     }
+    if (mode == UPD_XR) return;  // no reduction: gamma follows the preconditioner
     __shared__ double sh[32];
     double bt = block_dot_total(dot, sh);
     double total;
     if (grid_reduce(bt, partials, &st->ticket[1], &total))
-        finalize_gamma(st, total, mode, GammaFloor<T>::value);
+        finalize_gamma(st, total,
+                       mode == UPD_GZ_INIT ? UPD_INIT : (mode == UPD_GZ_STEP ? UPD_STEP : mode),
+                       GammaFloor<T>::value);
 }
 
 // out[s] = (Tout)(scale * f[i] * in[s]) on the entries of row i (G lanes per row)
@@ -868,7 +881,7 @@ template <class T>
 void launch_ydir(const Launch &L, long long count, Work<T> &w) {
     if (count <= 0) return;
     const int g = grid_for((count + Vec<T>::W - 1) / Vec<T>::W, L.grid_rows);
-    k_ydir_flat<T><<<g, kBlock, 0, L.stream>>>(count, w.R, w.Y, w.st);
+    k_ydir_flat<T><<<g, kBlock, 0, L.stream>>>(count, w.Z ? w.Z : w.R, w.Y, w.st);
     note_launch();
 }
 
@@ -877,7 +890,7 @@ void launch_update(const Launch &L, long long count, Work<T> &w, int mode) {
     if (count <= 0) return;
     const int g = grid_for((count + Vec<T>::W - 1) / Vec<T>::W, L.grid_rows);
     k_update_flat<T><<<g, kBlock, 0, L.stream>>>(count, w.R, w.Y, w.Yb, w.X, w.st, w.partials,
-                                                  mode);
+                                                  mode, w.Z);
     note_launch();
 }
 

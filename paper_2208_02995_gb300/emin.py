@@ -30,6 +30,7 @@ EMIN_ERR_STATE = -9
 EMIN_FP64 = 0
 EMIN_MIXED = 1
 EMIN_JACOBI = 0
+EMIN_SGS = 1
 EMIN_RANK_STRICT = 0
 EMIN_RANK_PINV = 1
 
@@ -323,18 +324,20 @@ def emin_destroy(h):
 # ---------------------------------------------------------------------------
 class Context:
     """Owns one library context.  ``precision``: "fp64" or "mixed";
+    ``precond``: "jacobi" (M_1) or "sgs" (the projected block SGS, M_2);
     ``stream``: a torch.cuda.Stream or raw cudaStream_t (int), default the
     current torch stream when inputs are CUDA tensors, else the legacy
     default stream."""
 
     def __init__(self, prob=None, *, n=None, nc=None, k=None, arrays=None, precision="fp64",
-                 rank_policy="strict", stream=None, on_device=None):
+                 rank_policy="strict", stream=None, on_device=None, precond="jacobi"):
         if prob is not None:
             n, nc, k, arrays = prob.n, prob.nc, prob.k, prob.arrays()
         self.n, self.nc, self.k = int(n), int(nc), int(k)
         opts = emin_default_opts()
         opts.precision = {"fp64": EMIN_FP64, "mixed": EMIN_MIXED}[precision]
         opts.rank_policy = {"strict": EMIN_RANK_STRICT, "pinv": EMIN_RANK_PINV}[rank_policy]
+        opts.precond = {"jacobi": EMIN_JACOBI, "sgs": EMIN_SGS}[precond]
         if on_device is None:
             on_device = _is_cuda_tensor(arrays[0])
         if stream is None and on_device:
@@ -344,6 +347,7 @@ class Context:
             stream = stream.cuda_stream
         opts.stream = stream
         self.precision = precision
+        self.precond = precond
         self.h = emin_create(self.n, self.nc, self.k, *arrays, opts=opts,
                              inputs_on_device=on_device)
         self.nnz_a, self.nnz_p = emin_sizes(self.h)
