@@ -55,6 +55,9 @@ def parse():
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-e2e", action="store_true")
     ap.add_argument("--no-tau", action="store_true", help="skip the time-to-tau measurement")
+    ap.add_argument("--no-sgs", action="store_true", help="skip the SGS preconditioner summary")
+    ap.add_argument("--precond", choices=["jacobi", "sgs"], default="jacobi",
+                    help="preconditioner of the timed runs (the headline is Jacobi)")
     ap.add_argument("--precision", choices=["both", "mixed", "fp64"], default="both",
                     help="profiling aid: run one arm only (the JSON line needs both)")
     ap.add_argument("--workload", type=int, default=WORKLOAD,
@@ -270,7 +273,7 @@ def run_ours(args, dist):
     precs = ("mixed", "fp64") if args.precision == "both" else (args.precision,)
     for prec in precs:
         with torch.cuda.stream(stream):
-            ctx = Context(prob, precision=prec, stream=stream)
+            ctx = Context(prob, precision=prec, stream=stream, precond=args.precond)
             out = torch.empty(prob.nnz_p, dtype=torch.float64, device="cuda")
         clocks = Clocks(dist.local) if prec == "mixed" else None
         l0 = emin_timing(ctx.h)["total_launches"]
@@ -296,7 +299,8 @@ def run_ours(args, dist):
         ctx.close()
     if args.precision != "both" or args.workload != WORKLOAD:
         r = results[precs[0]]
-        return {"workload": prob.name, "precision": precs[0], "iters": iters,
+        return {"workload": prob.name, "precision": precs[0], "precond": args.precond,
+                "iters": iters,
                 "ms_per_step": r["ms"] / args.steps,
                 "kprod_avg_us": r["kprod_avg_us"], "kernel_ms": r["kernel_share"],
                 "gpu_launches": r["gpu_launches"]}
@@ -383,6 +387,8 @@ def run_ours(args, dist):
     }
     if not args.no_tau:
         line["time_to_tau"] = time_to_tau(prob, stream)
+    if not args.no_sgs:
+        line["sgs"] = sgs_summary(prob, stream, dist)
     if dist.world == 1 and not args.no_cpu_baseline and dist.rank == 0:
         line["cpu_baseline"] = cpu_baseline(prob)
     return line
@@ -392,7 +398,39 @@ TAUS = (0.1, 1e-3, 1e-6)
 TAU_MAXIT = 200
 
 
-def time_to_tau(prob, stream, reps=5, warm=2):
+def sgs_summary(prob, stream, dist, steps=20, warm=3):
+    """The projected block SGS preconditioner (M_2) beside Jacobi (M_1): the
+    same timed step (set-up + 20 iterations + P) in both precisions, the
+    energy reached after 5, 10 and 20 iterations with each preconditioner
+    (FP64), and the time to the energy criterion with M_2."""
+    import torch
+
+    from paper_2208_02995_gb300.emin import Context
+    out = {"step": "set-up + 20 iterations + final P, as the headline"}
+    for prec in ("mixed", "fp64"):
+        with torch.cuda.stream(stream):
+            ctx = Context(prob, precision=prec, stream=stream, precond="sgs")
+            P = torch.empty(prob.nnz_p, dtype=torch.float64, device="cuda")
+        ms = time_steps(ctx, P, steps, warm, stream, dist, ITERS) / steps
+        out[prec] = {"iterations_per_s": ITERS / (ms / 1e3), "ms_per_step": ms}
+        ctx.close()
+    energy = {}
+    for pc in ("jacobi", "sgs"):
+        with torch.cuda.stream(stream):
+            ctx = Context(prob, precision="fp64", stream=stream, precond=pc)
+        rows = {"0": ctx.energy()}
+        for its in (5, 10, 20):
+            ctx.reset()
+            ctx.iterate(its)
+            rows[str(its)] = ctx.energy()
+        energy[pc] = rows
+        ctx.close()
+    out["energy_fp64"] = energy
+    out["time_to_tau"] = time_to_tau(prob, stream, precond="sgs")
+    return out
+
+
+def time_to_tau(prob, stream, reps=5, warm=2, precond="jacobi"):
     """Time to the energy stop test of Eq. (relRed): one whole minimisation
     (set-up, iterations until dE_k < tau dE_1 with at most TAU_MAXIT, P) per
     sample, CUDA events on the library's stream, for the paper's default
@@ -404,7 +442,7 @@ def time_to_tau(prob, stream, reps=5, warm=2):
            "stop test + P), mean of 5 after 2 warm-up", "samples": reps}
     for prec in ("mixed", "fp64"):
         with torch.cuda.stream(stream):
-            ctx = Context(prob, precision=prec, stream=stream)
+            ctx = Context(prob, precision=prec, stream=stream, precond=precond)
             P = torch.empty(prob.nnz_p, dtype=torch.float64, device="cuda")
         rows = []
         for tau in TAUS:

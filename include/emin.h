@@ -67,8 +67,9 @@ enum { EMIN_FP64 = 0,   /* every step in IEEE double                           *
  * increasing order), applied as z = Pi_B M_SGS^{-1} r.  EMIN_SGS builds a
  * plan on the host at create (copies of both patterns; time and memory grow
  * with the products inside the column blocks) and fails with EMIN_ERR_ARG
- * when one column of P has more than 65,535 rows or a group of columns with
- * the same rows needs more than 200 KB of shared memory. */
+ * when one column of P has more than 65,535 rows or more than 65,535
+ * couplings in one sweep, or when the values of one group of columns with
+ * the same rows need more than 96 KB (emin_last_error says which). */
 enum { EMIN_JACOBI = 0, EMIN_SGS = 1 };
 enum { EMIN_RANK_STRICT = 0, EMIN_RANK_PINV = 1 };
 

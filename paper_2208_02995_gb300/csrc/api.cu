@@ -53,12 +53,10 @@ struct emin_ctx {
     int ntiles = 0;
     // projected block SGS plan (EMIN_SGS), built once per context
     int sgs_ngroups = 0, sgs_cap = 0, sgs_gmax = 0;
-    long long sgs_nrows = 0, sgs_nf = 0, sgs_nb = 0;
-    int *sgs_hdr = nullptr, *sgs_rpos = nullptr, *sgs_flvl = nullptr, *sgs_blvl = nullptr;
-    int *sgs_foptr = nullptr, *sgs_boptr = nullptr, *sgs_fa = nullptr, *sgs_ba = nullptr;
-    int *sgs_fgrow = nullptr, *sgs_bgrow = nullptr;
-    unsigned short *sgs_frow = nullptr, *sgs_brow = nullptr, *sgs_fidx = nullptr,
-                   *sgs_bidx = nullptr;
+    long long sgs_nf = 0, sgs_nb = 0, sgs_stage32 = 0, sgs_stage64 = 0;
+    int *sgs_hdr = nullptr, *sgs_rpos = nullptr;
+    int *sgs_fown = nullptr, *sgs_fa = nullptr, *sgs_bown = nullptr, *sgs_ba = nullptr;
+    unsigned short *sgs_blob = nullptr;
     float *sgs_fval32 = nullptr, *sgs_bval32 = nullptr;
     double *sgs_fval64 = nullptr, *sgs_bval64 = nullptr;
     double *Pstar = nullptr, *t64c = nullptr;
@@ -186,19 +184,13 @@ SgsOps<T> sgs_ops(const emin_ctx *c, const T *fval, const T *bval) {
     SgsOps<T> s;
     if (c->opts.precond != EMIN_SGS || c->sgs_ngroups <= 0) return s;
     s.ngroups = c->sgs_ngroups;
-    s.nrows = c->sgs_nrows;
     s.cap = c->sgs_cap;
     s.gmax = c->sgs_gmax;
+    s.stage32 = c->sgs_stage32;
+    s.stage64 = c->sgs_stage64;
     s.hdr = c->sgs_hdr;
     s.rpos = c->sgs_rpos;
-    s.flvl = c->sgs_flvl;
-    s.foptr = c->sgs_foptr;
-    s.blvl = c->sgs_blvl;
-    s.boptr = c->sgs_boptr;
-    s.frow = c->sgs_frow;
-    s.fidx = c->sgs_fidx;
-    s.brow = c->sgs_brow;
-    s.bidx = c->sgs_bidx;
+    s.blob = reinterpret_cast<const uint4 *>(c->sgs_blob);
     s.fval = fval;
     s.bval = bval;
     return s;
@@ -255,8 +247,7 @@ int start_pcg(emin_ctx *c, const Ops<T> &o, Work<T> &w, const T *x0) {
     if (o.sgs.ngroups > 0) {
         // z~_0 = Pi (L^ + I)^{-T} (L^ + I)^{-1} r~_0, gamma_0 = <r~, z~>
         launch_sgs_sweep<T>(c->L, o.sgs, w.R, w.Z, w.st);
-        launch_project<T>(c->L, o, w.Z, T(1));
-        launch_update<T>(c->L, c->nnz_p, w, UPD_GZ_INIT);
+        launch_sgs_finish<T>(c->L, o, w, 1, c->nnz_p);
     } else {
         launch_update<T>(c->L, c->nnz_p, w, UPD_INIT);
     }
@@ -290,11 +281,11 @@ int build_sgs(emin_ctx *c) {
     const int st = build_sgs_plan(n, c->nc, Ap.data(), Aj.data(), Pp.data(), Pj.data(), h);
     if (st != EMIN_OK) {
         std::snprintf(g_last_error, sizeof(g_last_error),
-                      "SGS plan: a column of P has more than 65535 rows or an invalid index");
+                      "SGS plan: a column of P with more than 65535 rows or couplings");
         return st;
     }
     // one group's block must fit the shared memory of one block of one warp
-    if ((long long)h.cap * (long long)sizeof(double) > 200LL * 1024) {
+    if (((long long)h.cap * (long long)sizeof(double) + 15) / 16 * 16 > 96LL * 1024) {
         std::snprintf(g_last_error, sizeof(g_last_error),
                       "SGS plan: a column group of %d values exceeds shared memory", h.cap);
         return EMIN_ERR_ARG;
@@ -302,22 +293,16 @@ int build_sgs(emin_ctx *c) {
     c->sgs_ngroups = h.ngroups;
     c->sgs_cap = h.cap;
     c->sgs_gmax = h.gmax;
-    c->sgs_nrows = (long long)h.rpos.size();
+    c->sgs_stage32 = h.stage32;
+    c->sgs_stage64 = h.stage64;
     EMIN_TRY(upload(c, &c->sgs_hdr, h.hdr));
     EMIN_TRY(upload(c, &c->sgs_rpos, h.rpos));
-    EMIN_TRY(upload(c, &c->sgs_flvl, h.flvl));
-    EMIN_TRY(upload(c, &c->sgs_blvl, h.blvl));
-    EMIN_TRY(upload(c, &c->sgs_foptr, h.foptr));
-    EMIN_TRY(upload(c, &c->sgs_boptr, h.boptr));
+    EMIN_TRY(upload(c, &c->sgs_blob, h.blob));
+    EMIN_TRY(upload(c, &c->sgs_fown, h.fown));
     EMIN_TRY(upload(c, &c->sgs_fa, h.fa));
+    EMIN_TRY(upload(c, &c->sgs_bown, h.bown));
     EMIN_TRY(upload(c, &c->sgs_ba, h.ba));
-    EMIN_TRY(upload(c, &c->sgs_fgrow, h.fgrow));
-    EMIN_TRY(upload(c, &c->sgs_bgrow, h.bgrow));
-    EMIN_TRY(upload(c, &c->sgs_frow, h.frow));
-    EMIN_TRY(upload(c, &c->sgs_brow, h.brow));
-    EMIN_TRY(upload(c, &c->sgs_fidx, h.fidx));
-    EMIN_TRY(upload(c, &c->sgs_bidx, h.bidx));
-    const long long nf = (long long)h.fidx.size(), nb = (long long)h.bidx.size();
+    const long long nf = (long long)h.fa.size(), nb = (long long)h.ba.size();
     if (c->opts.precision == EMIN_MIXED) {
         EMIN_TRY(dalloc(c, &c->sgs_fval32, nf));
         EMIN_TRY(dalloc(c, &c->sgs_bval32, nb));
@@ -334,8 +319,8 @@ int build_sgs(emin_ctx *c) {
 template <class T>
 void form_sgs_values(emin_ctx *c, T *fval, T *bval) {
     if (c->opts.precond != EMIN_SGS || c->sgs_ngroups <= 0) return;
-    launch_sgs_values<T>(c->L, sgs_ops<T>(c, fval, bval), c->sgs_fgrow, c->sgs_bgrow, c->sgs_fa,
-                         c->sgs_ba, c->Aj, c->Av, c->dsq, fval, bval);
+    launch_sgs_values<T>(c->L, c->sgs_fown, c->sgs_fa, c->sgs_nf, c->sgs_bown, c->sgs_ba,
+                         c->sgs_nb, c->Aj, c->Av, c->dsq, fval, bval);
 }
 
 // A^ and q in double (the FP64 path, or the adjoint of a mixed context)
@@ -654,8 +639,7 @@ int launch_iterations(emin_ctx *c, const Ops<T> &o, Work<T> &w, int n_iters, boo
             // projected SGS: the step, then z~ = Pi M^-1 r~ and gamma = <r~, z~>
             launch_update<T>(c->L, c->nnz_p, w, UPD_XR);
             launch_sgs_sweep<T>(c->L, o.sgs, w.R, w.Z, w.st);
-            launch_project<T>(c->L, o, w.Z, T(1));
-            launch_update<T>(c->L, c->nnz_p, w, UPD_GZ_STEP);
+            launch_sgs_finish<T>(c->L, o, w, 0, c->nnz_p);
         } else {
             launch_update<T>(c->L, c->nnz_p, w, UPD_STEP);
         }

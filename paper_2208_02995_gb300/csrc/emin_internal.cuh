@@ -90,19 +90,19 @@ struct Work {
 };
 
 // The projected block SGS plan on the device (see sgs.cu): per group a
-// header of 8 ints (rows m, columns G, first plan row r0, forward levels
-// start / count, backward levels start / count, first column); per plan row
-// the position of its first entry; per sweep the rows in level order (local
-// index), the level boundaries, each row's couplings (local index, A^ value).
+// header of 12 ints (rows m, columns G, first plan row r0, index blob offset
+// and length in 16-byte units, first forward / backward coupling, coupling
+// counts, level counts, first column), per plan row the position of its
+// first entry, the uint16 index blobs, and the coupling values A^ of both
+// sweeps in group order.
 template <class T>
 struct SgsOps {
     int ngroups = 0;
-    long long nrows = 0;  // plan rows (sum of the groups' rows)
-    int cap = 0;          // largest m * G (shared memory per warp, in values)
-    int gmax = 0;         // largest G
+    int cap = 0;                 // largest m * G
+    int gmax = 0;                // largest G
+    long long stage32 = 0, stage64 = 0;  // largest staged group (bytes, float / double)
     const int *hdr = nullptr, *rpos = nullptr;
-    const int *flvl = nullptr, *foptr = nullptr, *blvl = nullptr, *boptr = nullptr;
-    const unsigned short *frow = nullptr, *fidx = nullptr, *brow = nullptr, *bidx = nullptr;
+    const uint4 *blob = nullptr;
     const T *fval = nullptr, *bval = nullptr;
 };
 
@@ -239,15 +239,19 @@ int pk_blocks_per_sm(int double_precision);
 // projected block SGS (sgs.cu)
 struct SgsHost {
     int ngroups = 0, cap = 0, gmax = 0;
-    std::vector<int> hdr, rpos, flvl, blvl, foptr, boptr, fa, ba, fgrow, bgrow;
-    std::vector<unsigned short> frow, brow, fidx, bidx;
+    long long stage32 = 0, stage64 = 0;
+    std::vector<int> hdr, rpos, fown, fa, bown, ba;
+    std::vector<unsigned short> blob;
 };
 int build_sgs_plan(int n, int nc, const int *Ap, const int *Aj, const int *Pp, const int *Pj,
                    SgsHost &out);
 template <class T>
-void launch_sgs_values(const Launch &L, const SgsOps<T> &s, const int *fgrow, const int *bgrow,
-                       const int *fa, const int *ba, const int *Aj, const double *Av,
-                       const double *dsq, T *fval, T *bval);
+void launch_sgs_values(const Launch &L, const int *fown, const int *fa, long long nf,
+                       const int *bown, const int *ba, long long nb, const int *Aj,
+                       const double *Av, const double *dsq, T *fval, T *bval);
+// z~ <- Pi z~ and gamma = <r~, z~> after the sweep (init: gamma_0)
+template <class T>
+void launch_sgs_finish(const Launch &L, const Ops<T> &o, Work<T> &w, int init, long long nnz_p);
 template <class T>
 void launch_sgs_sweep(const Launch &L, const SgsOps<T> &s, const T *R, T *Z, const DevState *st);
 void set_adjoint_attributes();
