@@ -28,7 +28,7 @@ import numpy as np
 __all__ = [
     "Problem", "splitmix64", "uniform01", "normal",
     "poisson2d", "diffusion3d_fv", "ring1d", "aniso3d", "elasticity3d",
-    "random_problem", "config", "CONFIG_NAMES",
+    "random_problem", "strength", "cf_split", "classical", "config", "CONFIG_NAMES",
 ]
 
 # ---------------------------------------------------------------------------
@@ -488,6 +488,110 @@ def random_problem(n: int = 40, nc: int = 12, k: int = 1, a_per_row: int = 4,
 # ---------------------------------------------------------------------------
 # named workloads
 # ---------------------------------------------------------------------------
+# ---------------------------------------------------------------------------
+# classical form P = [W; I] (Section 2): C/F splitting, strength of
+# connection, pattern growth S^k P0 (Eq. (enlPatt))
+# ---------------------------------------------------------------------------
+def strength(prob: Problem, theta: float = 0.25):
+    """Classical strength of connection of an M-matrix-like A: j is a strong
+    dependency of i if -a_ij >= theta max_(l != i) (-a_il).  Returns S as a
+    boolean CSR (rowptr, col) without the diagonal, columns sorted."""
+    n = prob.n
+    rows = np.repeat(np.arange(n), np.diff(prob.A_rowptr))
+    off = prob.A_col != rows
+    neg = np.where(off, -prob.A_val, -np.inf)
+    mx = np.full(n, -np.inf)
+    np.maximum.at(mx, rows, neg)
+    strong = off & (neg >= theta * mx[rows]) & (neg > 0)
+    cnt = np.bincount(rows[strong], minlength=n)
+    Sp = np.zeros(n + 1, dtype=np.int64)
+    np.cumsum(cnt, out=Sp[1:])
+    return Sp, prob.A_col[strong].astype(np.int64)
+
+
+def cf_split(prob: Problem, Sp, Sj, seed: int = 7):
+    """C/F splitting: a maximal independent set of the symmetrised strength
+    graph, chosen in rounds (a point joins C when its priority beats every
+    undecided neighbour; its neighbours become F), with priorities = number
+    of points that depend strongly on it plus a seeded fraction.  Returns a
+    boolean C mask."""
+    n = prob.n
+    rows = np.repeat(np.arange(n), np.diff(Sp))
+    ei = np.concatenate([rows, Sj])
+    ej = np.concatenate([Sj, rows])
+    pri = np.bincount(Sj, minlength=n).astype(np.float64) + uniform01(seed, n)
+    state = np.zeros(n, dtype=np.int8)  # 0 undecided, 1 C, 2 F
+    state[np.bincount(ei, minlength=n) == 0] = 1  # isolated points are C
+    while (state == 0).any():
+        und = state == 0
+        live = und[ei] & und[ej]
+        best = np.full(n, -1.0)
+        np.maximum.at(best, ei[live], pri[ej[live]])
+        newc = und & (pri > best)
+        state[newc] = 1
+        nb = ej[newc[ei]]
+        state[nb[state[nb] == 0]] = 2
+    return state == 1
+
+
+def classical(base: Problem, theta: float = 0.25, grow: int = 1, seed: int = 7,
+              iters: int = 10) -> Problem:
+    """The classical form P = [W; I] on the operator of ``base`` (k = 1,
+    near kernel B = 1): C/F splitting from the strength of connection S,
+    tentative pattern P0 = identity on C rows and the strong C dependencies
+    on F rows, grown to P = S^grow P0 on the F rows (Eq. (enlPatt)), C rows
+    kept as identity rows.  P0 values: 1 on C rows, equal weights summing to
+    1 on an F row's strong C dependencies, so that P0 B_c = B with B_c = B(C)
+    = 1.  A C row has one entry, so its constraint fixes it: only W moves,
+    and mask_P(A P0) carries f = -A_fc of Eq. (11blk) into the residual."""
+    n = base.n
+    Sp, Sj = strength(base, theta)
+    isC = cf_split(base, Sp, Sj, seed)
+    cidx = np.full(n, -1, dtype=np.int64)
+    cidx[isC] = np.arange(int(isC.sum()))
+    nc = int(isC.sum())
+    rows = np.repeat(np.arange(n), np.diff(Sp))
+    # P0 pattern: C rows {own}, F rows {strong C dependencies}
+    sc = isC[Sj]
+    p0_rows = np.concatenate([np.nonzero(isC)[0], rows[sc]])
+    p0_cols = np.concatenate([cidx[isC], cidx[Sj[sc]]])
+    f_nc = np.bincount(rows[sc], minlength=n)
+    lone = (~isC) & (f_nc == 0)  # F points with no strong C dependency: any C neighbour
+    if lone.any():
+        arow = np.repeat(np.arange(n), np.diff(base.A_rowptr))
+        m = lone[arow] & isC[base.A_col] & (base.A_col != arow)
+        p0_rows = np.concatenate([p0_rows, arow[m]])
+        p0_cols = np.concatenate([p0_cols, cidx[base.A_col[m]]])
+    key = np.unique(p0_rows * nc + p0_cols)
+    p0_rows, p0_cols = key // nc, key % nc
+    # growth on F rows: row i gathers the P0 columns of its strong dependencies
+    pat_r, pat_c = p0_rows, p0_cols
+    for _ in range(grow):
+        ptr = np.zeros(n + 1, dtype=np.int64)
+        np.cumsum(np.bincount(pat_r, minlength=n), out=ptr[1:])
+        fr = ~isC[rows]
+        src_i, src_l = rows[fr], Sj[fr]
+        cnt = ptr[src_l + 1] - ptr[src_l]
+        rep_i = np.repeat(src_i, cnt)
+        starts = np.repeat(ptr[src_l], cnt)
+        offs = np.arange(int(cnt.sum())) - np.repeat(np.cumsum(cnt) - cnt, cnt)
+        new_c = pat_c[starts + offs]
+        key = np.unique(np.concatenate([pat_r * nc + pat_c, rep_i * nc + new_c]))
+        pat_r, pat_c = key // nc, key % nc
+    P_rowptr = np.zeros(n + 1, dtype=np.int64)
+    np.cumsum(np.bincount(pat_r, minlength=n), out=P_rowptr[1:])
+    P_col = pat_c.astype(np.int32)
+    # P0 values on the grown pattern
+    own = np.zeros(len(pat_r))
+    in0 = np.isin(pat_r * nc + pat_c, p0_rows * nc + p0_cols)
+    cnt0 = np.bincount(p0_rows, minlength=n).astype(np.float64)
+    own[in0] = 1.0 / cnt0[pat_r[in0]]
+    return Problem(f"classical_{base.name}", n, nc, 1, base.A_rowptr, base.A_col, base.A_val,
+                   P_rowptr.astype(np.int32), P_col, own, np.ones((n, 1)), np.ones((nc, 1)),
+                   iters, {"kind": "classical", "base": base.name, "theta": theta,
+                           "grow": grow, "seed": seed, "cpoints": np.nonzero(isC)[0]})
+
+
 CONFIG_NAMES = {
     1: "2D 5-point Poisson 64x64, k=1, 2x2 aggregates, 10 iterations, FP64",
     2: "3D 7-point FV diffusion 128^3, log-normal kappa (sigma=2, seed 2), k=1, "

@@ -46,6 +46,9 @@ SMALL = [
     I.random_problem(300, 60, 1, seed=1, wide_rows=(3, 77), wide=40),
     I.random_problem(200, 90, 3, p_per_row=7, seed=2, wide_rows=(5,), wide=80),
     I.random_problem(150, 400, 2, p_per_row=5, seed=3, wide_rows=(9,), wide=300),
+    I.classical(I.diffusion3d_fv(16, 3)),     # P = [W; I], rows of W up to 12
+    I.classical(I.aniso3d(12, 1e-3, 2)),      # semi-coarsening by the strength filter
+    I.classical(I.poisson2d(40, 2), grow=2),  # pattern grown twice
 ]
 SMALL_IDS = [p.name for p in SMALL]
 
@@ -288,6 +291,29 @@ def test_workload2_full_size(precision):
         Eref = o.energy(ref["P"])
         assert abs(c.energy() - Eref) <= MIXED_E_TOL * abs(Eref)
         assert relf(P, ref["P"]) <= 1e-4
+    assert o.constraint_error(P) <= CONSTRAINT_TOL
+
+
+@pytest.mark.parametrize("precision", ["fp64", "mixed"])
+def test_classical_fv64(precision):
+    """The classical form P = [W; I] on the heterogeneous FV operator at 64^3
+    (262,144 rows; C/F splitting, strength filter, one growth step): 15
+    iterations against the oracle; the C rows stay identity rows."""
+    prob = I.classical(I.diffusion3d_fv(64, 3))
+    o = Oracle(prob)
+    ref = o.minimize(15, 0.0)
+    c = ctx(prob, precision)
+    done, _ = c.iterate(15, 0.0)
+    # the float path may stop earlier, at its convergence floor of gamma
+    assert done == ref["applied"] if precision == "fp64" else 0 < done <= ref["applied"]
+    P = c.get_p()
+    if precision == "fp64":
+        assert relf(P, ref["P"]) <= FP64_TOL
+    else:
+        Eref = o.energy(ref["P"])
+        assert abs(c.energy() - Eref) <= MIXED_E_TOL * abs(Eref)
+    C = prob.meta["cpoints"]
+    assert np.abs(P[prob.P_rowptr[C]] - 1.0).max() <= 1e-12
     assert o.constraint_error(P) <= CONSTRAINT_TOL
 
 

@@ -41,6 +41,9 @@ SMALL = [
     I.random_problem(300, 60, 1, seed=1, wide_rows=(3, 77), wide=40),
     I.random_problem(200, 90, 3, p_per_row=7, seed=2, wide_rows=(5,), wide=80),
     I.random_problem(150, 400, 2, p_per_row=5, seed=3, wide_rows=(9,), wide=300),
+    I.classical(I.diffusion3d_fv(16, 3)),     # P = [W; I], rows of W up to 12
+    I.classical(I.aniso3d(12, 1e-3, 2)),      # semi-coarsening by the strength filter
+    I.classical(I.poisson2d(40, 2), grow=2),  # pattern grown twice
 ]
 IDS = [p.name for p in SMALL]
 

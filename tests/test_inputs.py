@@ -113,3 +113,42 @@ def test_elasticity_blocks():
     P = _P(el).toarray()
     G = P.T @ P
     assert np.abs(G - np.eye(el.nc)).max() < 1e-12
+
+
+@pytest.mark.parametrize("base", [I.poisson2d(12, 2), I.aniso3d(7, 1e-3, 2),
+                                  I.diffusion3d_fv(9, 3)], ids=lambda p: p.name)
+def test_classical_form(base):
+    """P = [W; I]: C rows are identity rows (one entry, the point's own
+    coarse index, value 1), every F row of P0 sums to 1 (P0 B_c = B with
+    B = B_c = 1), and the F rows' pattern is the boolean product S P0_bar
+    of the strength matrix with the tentative pattern (Eq. (enlPatt))."""
+    p = I.classical(base, theta=0.25, grow=1)
+    n, nc = p.n, p.nc
+    C = p.meta["cpoints"]
+    isC = np.zeros(n, dtype=bool)
+    isC[C] = True
+    m = np.diff(p.P_rowptr)
+    assert np.all(m[isC] == 1)
+    assert np.array_equal(p.P_col[p.P_rowptr[C]], np.arange(nc))
+    assert np.all(p.P0_val[p.P_rowptr[C]] == 1.0)
+    assert np.all(m[~isC] >= 1)
+    rows = np.repeat(np.arange(n), m)
+    assert np.allclose(np.bincount(rows, weights=p.P0_val, minlength=n), 1.0)
+    # strength: -a_ij >= theta max_l -a_il (dense re-computation)
+    A = _A(p).toarray()
+    Sp, Sj = I.strength(p, 0.25)
+    S = np.zeros((n, n), dtype=bool)
+    S[np.repeat(np.arange(n), np.diff(Sp)), Sj] = True
+    for i in range(n):
+        off = -A[i].copy()
+        off[i] = -np.inf
+        mx = off.max()
+        ref = (off >= 0.25 * mx) & (off > 0)
+        assert np.array_equal(S[i], ref)
+    # pattern of the F rows = S P0_bar (dense boolean) united with P0_bar
+    P0bar = np.zeros((n, nc), dtype=bool)
+    P0bar[rows[p.P0_val != 0], p.P_col[p.P0_val != 0]] = True
+    grown = (S.astype(int) @ P0bar.astype(int) > 0) | P0bar
+    Pbar = np.zeros((n, nc), dtype=bool)
+    Pbar[rows, p.P_col] = True
+    assert np.array_equal(Pbar[~isC], grown[~isC])

@@ -21,6 +21,9 @@ TINY = [
     I.random_problem(30, 10, 1, seed=1),
     I.random_problem(30, 12, 2, p_per_row=6, seed=3),
     I.random_problem(24, 14, 3, p_per_row=7, seed=5, wide_rows=(3,), wide=14),
+    I.classical(I.poisson2d(7, 2)),
+    I.classical(I.aniso3d(5, 0.1, 2)),
+    I.classical(I.diffusion3d_fv(5, 3)),
 ]
 IDS = [p.name for p in TINY]
 
@@ -355,3 +358,43 @@ def test_backward_sgs_equals_jacobi(prob):
     assert np.abs(Us - Uj).max() <= 1e-9 * max(1, np.abs(Uj).max())
     assert np.abs(dAs - dAj).max() <= 1e-8 * max(1, np.abs(dAj).max())
     assert np.abs(dBs - dBj).max() <= 1e-8 * max(1, np.abs(dBj).max())
+
+
+def _full_w(base):
+    """The classical form with a full W pattern (every F row holds every
+    coarse column) on the operator of ``base``."""
+    p = I.classical(base)
+    n, nc = p.n, p.nc
+    isC = np.zeros(n, dtype=bool)
+    isC[p.meta["cpoints"]] = True
+    rows0 = np.repeat(np.arange(n), np.diff(p.P_rowptr))
+    P0 = np.zeros((n, nc))
+    P0[rows0, p.P_col] = p.P0_val
+    mask = np.zeros((n, nc), dtype=bool)
+    mask[~isC] = True
+    mask[isC, np.arange(nc)] = True
+    r, c = np.nonzero(mask)
+    Pp = np.zeros(n + 1, dtype=np.int32)
+    np.cumsum(np.bincount(r, minlength=n), out=Pp[1:])
+    return I.Problem(p.name + "_fullW", n, nc, 1, p.A_rowptr, p.A_col, p.A_val, Pp,
+                     c.astype(np.int32), P0[r, c], p.B, p.Bc, p.iters, p.meta), isC
+
+
+@pytest.mark.parametrize("base", [I.ring1d(24, 2), I.diffusion3d_fv(4, 2)],
+                         ids=lambda p: p.name)
+@pytest.mark.parametrize("precond", ["jacobi", "sgs"])
+def test_classical_full_pattern_is_ideal_prolongation(base, precond):
+    """With a full W pattern the energy minimiser of P = [W; I] is the ideal
+    prolongation W = -A_ff^{-1} A_fc (each column minimises p^T A p with its
+    C entry fixed, Eq. (minblk)); on a Neumann operator (A 1 = 0) it also
+    interpolates the constant, A_ff 1 + A_fc 1 = 0, so the constraint holds
+    and the constrained minimiser is the same.  The C rows, one entry each,
+    stay identity rows under the constraint."""
+    p, isC = _full_w(base)
+    o = Oracle(p, precond=precond)
+    P = o.minimize(800, 0.0)["P"]
+    A = KD.dense_A(p)
+    Wideal = -np.linalg.solve(A[np.ix_(~isC, ~isC)], A[np.ix_(~isC, isC)])
+    Pd = _dense_P(p, P)
+    assert np.abs(Pd[~isC] - Wideal).max() <= 1e-9 * max(1, np.abs(Wideal).max())
+    assert np.abs(Pd[isC] - np.eye(p.nc)).max() <= 1e-14
