@@ -179,6 +179,25 @@ int emin_backward(emin_ctx *ctx, const double *dL_dP, double *dL_dAval, double *
                   int max_adj_iters, double adj_tol, int on_device, int *adj_iters);
 
 /*
+ * Gradient of exactly n_iters steps (not in the paper): the vector-Jacobian
+ * product of the map (A values, B) -> P_n, P_n = the set-up's corrected P0
+ * (Algorithm 2) followed by n_iters steps of Algorithm 3 with the Jacobi
+ * preconditioner in double, for a forward that has not converged (for a
+ * converged one it approaches emin_backward).  Given dL/dP (nnz(P)) it
+ * returns dL_dAval (nnz(A), one value per stored entry, including the terms
+ * through the Jacobi scaling and the initial residual) and dL_dB (n x k,
+ * through the correction of P0).  The steps are run again in double from
+ * the set-up (the context's own iteration state is not used or changed);
+ * the iterates are checkpointed every ceil(sqrt(n_iters)) steps and each
+ * segment is recomputed before it is reversed, so memory grows with
+ * sqrt(n_iters) vectors on P's pattern.  Needs an EMIN_FP64 context with
+ * EMIN_JACOBI (else EMIN_ERR_ARG); A must be symmetric.  Either output may
+ * be NULL.  EMIN_ERR_BREAKDOWN if a step has y^T K y <= 0.
+ */
+int emin_backward_unrolled(emin_ctx *ctx, const double *dL_dP, int n_iters, double *dL_dAval,
+                           double *dL_dB, int on_device);
+
+/*
  * Statistics: dE_k of the computed iterations since the last (re)start
  * (up to cap values into dE_hist, may be NULL), their count, the number of
  * rank-deficient rows handled by EMIN_RANK_PINV, and the applied steps.

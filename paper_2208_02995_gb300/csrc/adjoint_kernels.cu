@@ -88,6 +88,66 @@ __global__ void k_axpby(long long count, double a, const double *__restrict__ x,
         y[q] = fma(a, x[q], b * y[q]);
 }
 
+// <x, y> into st->aux (deterministic last-block reduction).
+__global__ void __launch_bounds__(kBlock)
+k_dot_aux(long long count, const double *__restrict__ x, const double *__restrict__ y,
+          DevState *st, double *partials) {
+    double v = 0.0;
+    for (long long q = blockIdx.x * (long long)blockDim.x + threadIdx.x; q < count;
+         q += (long long)gridDim.x * blockDim.x)
+        v = fma(x[q], y[q], v);
+    __shared__ double sh[32];
+    const double bt = block_sum(v, sh);
+    double total;
+    if (grid_reduce(bt, partials, &st->ticket[2], &total)) st->aux = total;
+}
+
+// out[i] += scale * d_i^(-pw/2) * sum over row i of P of u v  (d_i^(-1/2) = dsq[i])
+__global__ void k_row_dot_acc(int n, const int *__restrict__ Pp, const double *__restrict__ u,
+                              const double *__restrict__ v, const double *__restrict__ dsq,
+                              int pw, double scale, double *__restrict__ out) {
+    for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < n; i += gridDim.x * blockDim.x) {
+        double t = 0.0;
+        for (int s = Pp[i]; s < Pp[i + 1]; ++s) t = fma(u[s], v[s], t);
+        double g = 1.0;
+        for (int q = 0; q < pw; ++q) g *= dsq[i];
+        out[i] += scale * g * t;
+    }
+}
+
+// Chain rule from A^ = D^{-1/2} A D^{-1/2} (d = diag A) to the stored values
+// of A, one thread per row i: with ghat the gradient with respect to A^,
+//   dL/da_e = ghat_e d_i^{-1/2} d_l^{-1/2}                   (e = (i, l))
+//   dL/dd_i = dext_i - 1/2 d_i^{-1} sum over the entries e of row i and
+//             their mirrors e' = (l, i) of ghat A^ (row and column factor),
+// and dL/dd_i is added to the diagonal entry.  A is symmetric with sorted
+// columns, so the mirror of (i, l) is found in row l by binary search.
+__global__ void k_grad_a(int n, const int *__restrict__ Ap, const int *__restrict__ Aj,
+                         const double *__restrict__ Av, const double *__restrict__ dsq,
+                         const double *__restrict__ ghat, const double *__restrict__ dext,
+                         double *__restrict__ gA) {
+    for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < n; i += gridDim.x * blockDim.x) {
+        const double di = dsq[i];
+        double t = 0.0;
+        for (int e = Ap[i]; e < Ap[i + 1]; ++e) {
+            const int l = Aj[e];
+            const double ahat = di * Av[e] * dsq[l];
+            t = fma(ghat[e], ahat, t);
+            int lo = Ap[l], hi = Ap[l + 1];
+            while (lo < hi) {
+                const int mid = (lo + hi) >> 1;
+                if (Aj[mid] < i) lo = mid + 1; else hi = mid;
+            }
+            if (lo < Ap[l + 1] && Aj[lo] == i) t = fma(ghat[lo], ahat, t);
+        }
+        const double dbar = dext[i] - 0.5 * di * di * t;
+        for (int e = Ap[i]; e < Ap[i + 1]; ++e) {
+            const int l = Aj[e];
+            gA[e] = ghat[e] * di * dsq[l] + (l == i ? dbar : 0.0);
+        }
+    }
+}
+
 }  // namespace
 
 void launch_outer(const Launch &L, int n, const int *Ap, const int *Aj, const int *Pp,
@@ -118,6 +178,29 @@ void launch_axpby(const Launch &L, long long count, double a, const double *x, d
                   double *y) {
     if (count <= 0) return;
     k_axpby<<<grid_for(count, L.grid_rows), kBlock, 0, L.stream>>>(count, a, x, b, y); note_launch();
+}
+
+void launch_dot_aux(const Launch &L, long long count, const double *x, const double *y,
+                    DevState *st, double *partials) {
+    k_dot_aux<<<grid_for(count > 0 ? count : 1, L.grid_rows), kBlock, 0, L.stream>>>(
+        count, x, y, st, partials);
+    note_launch();
+}
+
+void launch_row_dot_acc(const Launch &L, int n, const int *Pp, const double *u, const double *v,
+                        const double *dsq, int pw, double scale, double *out) {
+    if (n <= 0) return;
+    k_row_dot_acc<<<grid_for(n, L.grid_rows), kBlock, 0, L.stream>>>(n, Pp, u, v, dsq, pw, scale,
+                                                                      out);
+    note_launch();
+}
+
+void launch_grad_a(const Launch &L, int n, const int *Ap, const int *Aj, const double *Av,
+                   const double *dsq, const double *ghat, const double *dext, double *gA) {
+    if (n <= 0) return;
+    k_grad_a<<<grid_for(n, L.grid_rows), kBlock, 0, L.stream>>>(n, Ap, Aj, Av, dsq, ghat, dext,
+                                                                 gA);
+    note_launch();
 }
 
 void set_adjoint_attributes() {

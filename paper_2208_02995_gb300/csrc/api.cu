@@ -4,6 +4,8 @@
 // implicit adjoint.  All device work runs on the context's stream.
 #include <cuda_runtime.h>
 
+#include <cmath>
+
 #include <atomic>
 #include <cstdio>
 #include <cstring>
@@ -67,6 +69,9 @@ struct emin_ctx {
     Work<double> aux;   // stand-alone reductions (energy)
     // scratch
     double *t64a = nullptr, *t64b = nullptr, *tA = nullptr, *tmu = nullptr;
+    // unrolled adjoint: vectors on P's pattern (checkpoints, segment, work)
+    std::vector<double *> unr;
+    double *unr_ghat = nullptr, *unr_dext = nullptr, *unr_gA = nullptr;
     float *t32a = nullptr, *t32b = nullptr;
     int *dint = nullptr;       // [0] flags, [1] longest row of P, [2] rank-deficient rows
     DevState *hstate = nullptr;  // pinned mirror
@@ -252,6 +257,12 @@ int start_pcg(emin_ctx *c, const Ops<T> &o, Work<T> &w, const T *x0) {
         launch_update<T>(c->L, c->nnz_p, w, UPD_INIT);
     }
     return check_launch();
+}
+
+template <class T>
+int dalloc_once(emin_ctx *c, T **p, long long count) {
+    if (*p) return EMIN_OK;
+    return dalloc(c, p, count);
 }
 
 template <class T>
@@ -968,6 +979,198 @@ int emin_outer(emin_ctx *c, const double *U, const double *V, double *out, int o
     launch_outer(c->L, c->n, c->Ap, c->Aj, c->Pp, c->Pj, c->t64a, c->t64b, 1.0, c->tA, c->maxrow_p);
     EMIN_TRY(check_launch());
     EMIN_TRY(copy_out(c, out, c->tA, sizeof(double) * c->nnz_a, on_device));
+    return sync(c);
+}
+
+}  // extern "C"
+
+namespace {
+
+// the idx-th vector on P's pattern of the unrolled adjoint (allocated once)
+int unr_vec(emin_ctx *c, size_t idx, double **out) {
+    while (c->unr.size() <= idx) {
+        double *p = nullptr;
+        EMIN_TRY(dalloc(c, &p, c->nnz_p));
+        c->unr.push_back(p);
+    }
+    *out = c->unr[idx];
+    return EMIN_OK;
+}
+
+int read_aux(emin_ctx *c, const Work<double> &w, double *v) {
+    EMIN_TRY(cuda_status(cudaMemcpyAsync(v, &w.st->aux, sizeof(double), cudaMemcpyDeviceToHost,
+                                         c->stream)));
+    return sync(c);
+}
+
+// The gradient of exactly n_iters steps of Algorithm 3 (Jacobi, FP64) from
+// the set-up's P0, by reverse accumulation through the steps in the scaled
+// variables (r~ = D^{-1/2} r, y~ = D^{1/2} y, x~ = D^{1/2} dW on
+// A^ = D^{-1/2} A D^{-1/2}):
+//   gamma_k = <r~,r~>, beta_k = gamma_k/gamma_{k-1}, y~_k = r~_k + beta_k y~_{k-1},
+//   w~_k = Pi K^ y~_k, delta_k = <y~_k, w~_k>, alpha_k = gamma_k/delta_k,
+//   x~ += alpha_k y~_k, r~ -= alpha_k w~_k;  P = p0 + D^{-1/2} x~_n,
+// r~_0 = -Pi K^ D^{1/2} p0.  The adjoint of each step, from k = n-1 down:
+//   abar = <xbar, y~_k> - <rbar, w~_k>, dbar = -abar alpha_k / delta_k,
+//   wbar = -alpha_k rbar + dbar y~_k,
+//   ybar_k = (carry) + alpha_k xbar + dbar w~_k + K^ Pi wbar,
+//   ghat += mask_A((Pi wbar) y~_k^T),  betabar = <ybar_k, y~_{k-1}>,
+//   gammabar_k = (carry) + abar/delta_k + betabar/gamma_{k-1},
+//   rbar += ybar_k + 2 gammabar_k r~_k,  carries: beta_k ybar_k and
+//   -betabar gamma_k / gamma_{k-1}^2,
+// with xbar = D^{-1/2} dL/dP.  The iterates are checkpointed every
+// s = ceil(sqrt(n)) steps (r~_k and y~_{k-1}) and each segment is run forward
+// again before its steps are reversed: O(sqrt(n)) stored vectors.
+int unrolled_backward(emin_ctx *c, const double *dLdP, int n_iters, double *gA, double *gB) {
+    const Ops<double> o = iter_ops64(c);
+    Work<double> &w = c->adj;
+    const Launch &L = c->L;
+    const long long np = c->nnz_p, na = c->nnz_a;
+    const int n = c->n;
+    const int sgl = (int)std::ceil(std::sqrt((double)n_iters));
+    const int ncp = (n_iters + sgl - 1) / sgl;
+    // vectors: checkpoints r, y; segment r, y; pt0, xbar, rbar, ybar, wt, wb, pw, tmp, zero
+    size_t q = 0;
+    std::vector<double *> cpr(ncp), cpy(ncp), sr(sgl), sy(sgl);
+    for (int i = 0; i < ncp; ++i) EMIN_TRY(unr_vec(c, q++, &cpr[i]));
+    for (int i = 0; i < ncp; ++i) EMIN_TRY(unr_vec(c, q++, &cpy[i]));
+    for (int i = 0; i < sgl; ++i) EMIN_TRY(unr_vec(c, q++, &sr[i]));
+    for (int i = 0; i < sgl; ++i) EMIN_TRY(unr_vec(c, q++, &sy[i]));
+    double *pt0, *xbar, *rbar, *ybar, *wt, *wb, *pw, *tmp, *zero;
+    for (double **v : {&pt0, &xbar, &rbar, &ybar, &wt, &wb, &pw, &tmp, &zero})
+        EMIN_TRY(unr_vec(c, q++, v));
+    if (!c->unr_ghat) EMIN_TRY(dalloc(c, &c->unr_ghat, na));
+    if (!c->unr_dext) EMIN_TRY(dalloc(c, &c->unr_dext, n));
+    double *R = w.R, *Y = w.Y, *Yb = w.Yb, *X = w.X;
+    const size_t vb = sizeof(double) * np;
+    auto dcopy = [&](double *dst, const double *src) {
+        return cuda_status(cudaMemcpyAsync(dst, src, vb, cudaMemcpyDeviceToDevice, c->stream));
+    };
+    auto dot = [&](const double *x, const double *y, double *v) {
+        launch_dot_aux(L, np, x, y, w.st, w.partials);
+        return read_aux(c, w, v);
+    };
+    std::vector<double> gam(n_iters), bet(n_iters), del(n_iters), alp(n_iters);
+    // forward, keeping the scalars and the checkpoints
+    launch_row_scale<double, double>(L, n, c->Pp, c->lanes, c->dhalf, 1.0, c->P0, pt0);
+    launch_kprod<double>(L, o, pt0, R, 1, DOT_NONE, w, 0);
+    launch_axpby(L, np, 0.0, R, -1.0, R);
+    EMIN_TRY(cuda_status(cudaMemsetAsync(X, 0, vb, c->stream)));
+    EMIN_TRY(cuda_status(cudaMemsetAsync(Y, 0, vb, c->stream)));
+    EMIN_TRY(cuda_status(cudaMemsetAsync(zero, 0, vb, c->stream)));
+    for (int k = 0; k < n_iters; ++k) {
+        if (k % sgl == 0) {
+            EMIN_TRY(dcopy(cpr[k / sgl], R));
+            EMIN_TRY(dcopy(cpy[k / sgl], Y));
+        }
+        EMIN_TRY(dot(R, R, &gam[k]));
+        bet[k] = k ? gam[k] / gam[k - 1] : 0.0;
+        launch_axpby(L, np, 1.0, R, bet[k], Y);
+        launch_kprod<double>(L, o, Y, Yb, 1, DOT_AUX, w, 0);
+        EMIN_TRY(read_aux(c, w, &del[k]));
+        if (!(del[k] > 0.0) || !std::isfinite(del[k]) || !std::isfinite(gam[k]))
+            return EMIN_ERR_BREAKDOWN;
+        alp[k] = gam[k] / del[k];
+        launch_axpby(L, np, alp[k], Y, 1.0, X);
+        launch_axpby(L, np, -alp[k], Yb, 1.0, R);
+    }
+    // reverse: xbar = D^{-1/2} dL/dP; the output's dependence on d
+    launch_row_scale<double, double>(L, n, c->Pp, c->lanes, c->dsq, 1.0, dLdP, xbar);
+    EMIN_TRY(cuda_status(cudaMemsetAsync(c->unr_dext, 0, sizeof(double) * n, c->stream)));
+    launch_row_dot_acc(L, n, c->Pp, dLdP, X, c->dsq, 3, -0.5, c->unr_dext);
+    EMIN_TRY(cuda_status(cudaMemsetAsync(rbar, 0, vb, c->stream)));
+    EMIN_TRY(cuda_status(cudaMemsetAsync(ybar, 0, vb, c->stream)));
+    EMIN_TRY(cuda_status(cudaMemsetAsync(c->unr_ghat, 0, sizeof(double) * na, c->stream)));
+    double gcarry = 0.0;
+    for (int seg = ncp - 1; seg >= 0; --seg) {
+        const int k0 = seg * sgl, k1 = std::min(k0 + sgl, n_iters);
+        EMIN_TRY(dcopy(R, cpr[seg]));
+        EMIN_TRY(dcopy(Y, cpy[seg]));
+        for (int k = k0; k < k1; ++k) {  // the segment again, from its checkpoint
+            EMIN_TRY(dcopy(sr[k - k0], R));
+            launch_axpby(L, np, 1.0, R, bet[k], Y);
+            EMIN_TRY(dcopy(sy[k - k0], Y));
+            launch_kprod<double>(L, o, Y, Yb, 1, DOT_NONE, w, 0);
+            launch_axpby(L, np, -alp[k], Yb, 1.0, R);
+        }
+        for (int k = k1 - 1; k >= k0; --k) {
+            const double *yk = sy[k - k0], *rk = sr[k - k0];
+            const double *ykm1 = k == 0 ? zero : (k > k0 ? sy[k - k0 - 1] : cpy[seg]);
+            launch_kprod<double>(L, o, yk, wt, 1, DOT_NONE, w, 0);
+            double a1, a2;
+            EMIN_TRY(dot(xbar, yk, &a1));
+            EMIN_TRY(dot(rbar, wt, &a2));
+            const double abar = a1 - a2;
+            const double dbar = -abar * alp[k] / del[k];
+            EMIN_TRY(dcopy(wb, rbar));
+            launch_axpby(L, np, dbar, yk, -alp[k], wb);
+            EMIN_TRY(dcopy(pw, wb));
+            launch_project<double>(L, o, pw, 1.0);
+            launch_kprod<double>(L, o, pw, tmp, 0, DOT_NONE, w, 0);
+            launch_axpby(L, np, alp[k], xbar, 1.0, ybar);
+            launch_axpby(L, np, dbar, wt, 1.0, ybar);
+            launch_axpby(L, np, 1.0, tmp, 1.0, ybar);
+            launch_outer(L, n, c->Ap, c->Aj, c->Pp, c->Pj, pw, yk, 1.0, c->tA, c->maxrow_p);
+            launch_axpby(L, na, 1.0, c->tA, 1.0, c->unr_ghat);
+            double bbar = 0.0;
+            if (k > 0) EMIN_TRY(dot(ybar, ykm1, &bbar));
+            const double gbar = gcarry + abar / del[k] + (k > 0 ? bbar / gam[k - 1] : 0.0);
+            launch_axpby(L, np, 1.0, ybar, 1.0, rbar);
+            launch_axpby(L, np, 2.0 * gbar, rk, 1.0, rbar);
+            gcarry = k > 0 ? -bbar * gam[k] / (gam[k - 1] * gam[k - 1]) : 0.0;
+            launch_axpby(L, np, 0.0, ybar, bet[k], ybar);
+        }
+    }
+    // r~_0 = -Pi K^ p~0: p~0bar = -K^ Pi rbar, ghat += mask_A(-(Pi rbar) p~0^T)
+    EMIN_TRY(dcopy(pw, rbar));
+    launch_project<double>(L, o, pw, 1.0);
+    launch_kprod<double>(L, o, pw, tmp, 0, DOT_NONE, w, 0);  // tmp = -p~0bar
+    launch_outer(L, n, c->Ap, c->Aj, c->Pp, c->Pj, pw, pt0, -1.0, c->tA, c->maxrow_p);
+    launch_axpby(L, na, 1.0, c->tA, 1.0, c->unr_ghat);
+    // p0bar = dL/dP + D^{1/2} p~0bar;  p~0 = D^{1/2} p0 puts 1/2 d^{-1/2} <p~0bar, p0> on d
+    launch_row_scale<double, double>(L, n, c->Pp, c->lanes, c->dhalf, -1.0, tmp, pw);
+    launch_axpby(L, np, 1.0, dLdP, 1.0, pw);
+    launch_row_dot_acc(L, n, c->Pp, tmp, c->P0, c->dsq, 1, -0.5, c->unr_dext);
+    launch_grad_a(L, n, c->Ap, c->Aj, c->Av, c->dsq, c->unr_ghat, c->unr_dext, gA);
+    // the corrected P0 moves with B: dL/dB(i,:) = G_i^{-1} B_i^T p0bar_i
+    launch_lsq(L, n, c->k, c->Pp, c->Pj, c->Bc, c->Ginv, pw, gB);
+    return check_launch();
+}
+
+}  // namespace
+
+extern "C" {
+
+int emin_backward_unrolled(emin_ctx *c, const double *dL_dP, int n_iters, double *dL_dAval,
+                           double *dL_dB, int on_device) {
+    if (!c || !dL_dP || n_iters < 1) return EMIN_ERR_ARG;
+    DeviceGuard g(c->device);
+    if (c->sticky != EMIN_OK) return c->sticky;
+    if (c->opts.precond != EMIN_JACOBI || c->opts.precision != EMIN_FP64) {
+        std::snprintf(g_last_error, sizeof(g_last_error),
+                      "unrolled adjoint: needs an FP64 context with the Jacobi preconditioner");
+        return EMIN_ERR_ARG;
+    }
+    if (!c->adj.R) {
+        EMIN_TRY(alloc_work(c, c->adj, true));
+        if (!c->tA) EMIN_TRY(dalloc(c, &c->tA, c->nnz_a));
+        EMIN_TRY(dalloc(c, &c->tmu, (long long)c->n * c->k));
+        EMIN_TRY(dalloc(c, &c->Pstar, c->nnz_p));
+        if (!c->Ah64) EMIN_TRY(dalloc(c, &c->Ah64, c->nnz_a));
+        if (c->sell_ptr && !c->sa64) EMIN_TRY(dalloc(c, &c->sa64, c->nnz_sell));
+        if (c->k == 1 && !c->qv64) EMIN_TRY(dalloc(c, &c->qv64, c->nnz_p));
+    }
+    if (!c->have64) form_scaled64(c);
+    if (c->n == 0) return EMIN_OK;
+    EMIN_TRY(copy_in(c, c->t64b, dL_dP, sizeof(double) * c->nnz_p, on_device));
+    double *gA = nullptr;
+    if (!c->unr_ghat) EMIN_TRY(dalloc(c, &c->unr_ghat, c->nnz_a));
+    EMIN_TRY(dalloc_once(c, &c->unr_gA, c->nnz_a));
+    gA = c->unr_gA;
+    EMIN_TRY(unrolled_backward(c, c->t64b, n_iters, gA, c->tmu));
+    if (dL_dAval) EMIN_TRY(copy_out(c, dL_dAval, gA, sizeof(double) * c->nnz_a, on_device));
+    if (dL_dB)
+        EMIN_TRY(copy_out(c, dL_dB, c->tmu, sizeof(double) * (size_t)c->n * c->k, on_device));
     return sync(c);
 }
 

@@ -280,5 +280,15 @@ void launch_lsq(const Launch &L, int n, int k, const int *Pp, const int *Pj, con
                 const double *Ginv, const double *x, double *mu);
 void launch_axpby(const Launch &L, long long count, double a, const double *x, double b,
                   double *y);
+// <x, y> into st->aux
+void launch_dot_aux(const Launch &L, long long count, const double *x, const double *y,
+                    DevState *st, double *partials);
+// out[i] += scale * dsq_i^pw * sum over row i of P of u v
+void launch_row_dot_acc(const Launch &L, int n, const int *Pp, const double *u, const double *v,
+                        const double *dsq, int pw, double scale, double *out);
+// gradient with respect to the stored values of A from the one with
+// respect to A^ = D^{-1/2} A D^{-1/2} and the extra diagonal terms dext
+void launch_grad_a(const Launch &L, int n, const int *Ap, const int *Aj, const double *Av,
+                   const double *dsq, const double *ghat, const double *dext, double *gA);
 
 }  // namespace emin

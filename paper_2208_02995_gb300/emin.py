@@ -36,6 +36,7 @@ EMIN_RANK_PINV = 1
 
 SYMBOLS = ("emin_default_opts", "emin_create", "emin_set_values", "emin_reset", "emin_iterate",
            "emin_energy", "emin_get_p", "emin_kprod", "emin_outer", "emin_backward",
+           "emin_backward_unrolled",
            "emin_stats", "emin_sizes", "emin_strerror", "emin_destroy", "emin_set_timing",
            "emin_timing", "emin_masked_product_noalloc", "emin_last_error")
 
@@ -84,6 +85,7 @@ def lib():
         L.emin_kprod.argtypes = [_VP, _VP, _VP, _I, _I]
         L.emin_outer.argtypes = [_VP, _VP, _VP, _VP, _I]
         L.emin_backward.argtypes = [_VP, _VP, _VP, _VP, _I, _D, _I, ctypes.POINTER(_I)]
+        L.emin_backward_unrolled.argtypes = [_VP, _VP, _I, _VP, _VP, _I]
         L.emin_stats.argtypes = [_VP, _VP, _I, ctypes.POINTER(_I), ctypes.POINTER(_I),
                                  ctypes.POINTER(_I)]
         L.emin_sizes.argtypes = [_VP, ctypes.POINTER(ctypes.c_longlong),
@@ -265,6 +267,27 @@ def emin_backward(h, dL_dP, n_rows, k, max_adj_iters=200, adj_tol=0.0, want_A=Tr
     return dA, dB, it.value
 
 
+def emin_backward_unrolled(h, dL_dP, n_rows, k, n_iters, want_A=True, want_B=True):
+    """Gradient of exactly n_iters steps: returns (dL/dA values, dL/dB (n x k))."""
+    nnza, _ = emin_sizes(h)
+    keep = []
+    dev = _is_cuda_tensor(dL_dP)
+    if dev:
+        import torch
+        dA = torch.empty(nnza, dtype=torch.float64, device=dL_dP.device) if want_A else None
+        dB = torch.empty((n_rows, k), dtype=torch.float64, device=dL_dP.device) if want_B else None
+        pa = dA.data_ptr() if want_A else None
+        pb = dB.data_ptr() if want_B else None
+    else:
+        dA = np.empty(nnza) if want_A else None
+        dB = np.empty((n_rows, k)) if want_B else None
+        pa = dA.ctypes.data if want_A else None
+        pb = dB.ctypes.data if want_B else None
+    _check(lib().emin_backward_unrolled(h, _ptr(dL_dP, np.float64, keep), int(n_iters), pa, pb,
+                                        int(dev)), "emin_backward_unrolled")
+    return dA, dB
+
+
 def emin_stats(h, cap=4096):
     hist = np.zeros(max(cap, 1))
     nh, nd, na = _I(0), _I(0), _I(0)
@@ -389,6 +412,10 @@ class Context:
 
     def stats(self):
         return emin_stats(self.h)
+
+    def backward_unrolled(self, dLdP, n_iters):
+        """Gradient of exactly n_iters FP64 Jacobi steps (see emin.h)."""
+        return emin_backward_unrolled(self.h, dLdP, self.n, self.k, n_iters)
 
     def reset(self):
         emin_reset(self.h)
