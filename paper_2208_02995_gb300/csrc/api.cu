@@ -59,6 +59,14 @@ struct emin_ctx {
     int *sgs_hdr = nullptr, *sgs_rpos = nullptr;
     int *sgs_fown = nullptr, *sgs_fa = nullptr, *sgs_bown = nullptr, *sgs_ba = nullptr;
     unsigned short *sgs_blob = nullptr;
+    int sgs_nbatch = 0, sgs_bmax_u = 0, sgs_bmax_v = 0;
+    long long sgs_bnf = 0, sgs_bnb = 0;
+    int *sgs_cls_hdr = nullptr, *sgs_bat_hdr = nullptr, *sgs_bat_rpos = nullptr;
+    int *sgs_bat_fown = nullptr, *sgs_bat_fa = nullptr, *sgs_bat_bown = nullptr,
+        *sgs_bat_ba = nullptr;
+    unsigned short *sgs_cls_ptr = nullptr, *sgs_cls_idx = nullptr;
+    float *sgs_bfval32 = nullptr, *sgs_bbval32 = nullptr;
+    double *sgs_bfval64 = nullptr, *sgs_bbval64 = nullptr;
     float *sgs_fval32 = nullptr, *sgs_bval32 = nullptr;
     double *sgs_fval64 = nullptr, *sgs_bval64 = nullptr;
     double *Pstar = nullptr, *t64c = nullptr;
@@ -185,9 +193,20 @@ Ops<double> plain_ops64(const emin_ctx *c) {
 
 // the SGS plan with the values of one precision (an empty plan: Jacobi)
 template <class T>
-SgsOps<T> sgs_ops(const emin_ctx *c, const T *fval, const T *bval) {
+SgsOps<T> sgs_ops(const emin_ctx *c, const T *fval, const T *bval, const T *bfval,
+                  const T *bbval) {
     SgsOps<T> s;
-    if (c->opts.precond != EMIN_SGS || c->sgs_ngroups <= 0) return s;
+    if (c->opts.precond != EMIN_SGS || (c->sgs_ngroups <= 0 && c->sgs_nbatch <= 0)) return s;
+    s.nbatch = c->sgs_nbatch;
+    s.bmax_u = c->sgs_bmax_u;
+    s.bmax_v = c->sgs_bmax_v;
+    s.cls_hdr = c->sgs_cls_hdr;
+    s.bat_hdr = c->sgs_bat_hdr;
+    s.bat_rpos = c->sgs_bat_rpos;
+    s.cls_ptr = c->sgs_cls_ptr;
+    s.cls_idx = c->sgs_cls_idx;
+    s.bat_fval = bfval;
+    s.bat_bval = bbval;
     s.ngroups = c->sgs_ngroups;
     s.cap = c->sgs_cap;
     s.gmax = c->sgs_gmax;
@@ -206,7 +225,7 @@ Ops<double> iter_ops64(const emin_ctx *c) {
     Ops<double> o{c->n, c->nc, c->k, c->Ap, c->Aj, c->Ah64, c->Pp, c->Pj, c->Bc, c->Ginv,
                        c->qv64, c->sell_ptr, c->sa64, c->soff, c->smap, c->sw, nullptr, c->boff, c->blen, c->bmap, c->tile_map, c->ntiles,
                        c->maxrow_p, c->lanes};
-    o.sgs = sgs_ops<double>(c, c->sgs_fval64, c->sgs_bval64);
+    o.sgs = sgs_ops<double>(c, c->sgs_fval64, c->sgs_bval64, c->sgs_bfval64, c->sgs_bbval64);
     return o;
 }
 
@@ -214,7 +233,7 @@ Ops<float> iter_ops32(const emin_ctx *c) {
     Ops<float> o{c->n, c->nc, c->k, c->Ap, c->Aj, c->Ah32, c->Pp, c->Pj, c->Bc32, c->Ginv32,
                       c->qv32, c->sell_ptr, c->sa32, c->soff, c->smap, c->sw, c->spk32, c->boff, c->blen, c->bmap, c->tile_map, c->ntiles,
                       c->maxrow_p, c->lanes};
-    o.sgs = sgs_ops<float>(c, c->sgs_fval32, c->sgs_bval32);
+    o.sgs = sgs_ops<float>(c, c->sgs_fval32, c->sgs_bval32, c->sgs_bfval32, c->sgs_bbval32);
     return o;
 }
 
@@ -313,25 +332,46 @@ int build_sgs(emin_ctx *c) {
     EMIN_TRY(upload(c, &c->sgs_fa, h.fa));
     EMIN_TRY(upload(c, &c->sgs_bown, h.bown));
     EMIN_TRY(upload(c, &c->sgs_ba, h.ba));
+    c->sgs_nbatch = h.nbatch;
+    c->sgs_bmax_u = h.bmax_u;
+    c->sgs_bmax_v = h.bmax_v;
+    EMIN_TRY(upload(c, &c->sgs_cls_hdr, h.cls_hdr));
+    EMIN_TRY(upload(c, &c->sgs_bat_hdr, h.bat_hdr));
+    EMIN_TRY(upload(c, &c->sgs_bat_rpos, h.bat_rpos));
+    EMIN_TRY(upload(c, &c->sgs_bat_fown, h.bat_fown));
+    EMIN_TRY(upload(c, &c->sgs_bat_fa, h.bat_fa));
+    EMIN_TRY(upload(c, &c->sgs_bat_bown, h.bat_bown));
+    EMIN_TRY(upload(c, &c->sgs_bat_ba, h.bat_ba));
+    EMIN_TRY(upload(c, &c->sgs_cls_ptr, h.cls_ptr));
+    EMIN_TRY(upload(c, &c->sgs_cls_idx, h.cls_idx));
+    c->sgs_bnf = (long long)h.bat_fa.size();
+    c->sgs_bnb = (long long)h.bat_ba.size();
     const long long nf = (long long)h.fa.size(), nb = (long long)h.ba.size();
     if (c->opts.precision == EMIN_MIXED) {
         EMIN_TRY(dalloc(c, &c->sgs_fval32, nf));
         EMIN_TRY(dalloc(c, &c->sgs_bval32, nb));
+        EMIN_TRY(dalloc(c, &c->sgs_bfval32, c->sgs_bnf));
+        EMIN_TRY(dalloc(c, &c->sgs_bbval32, c->sgs_bnb));
     } else {
         EMIN_TRY(dalloc(c, &c->sgs_fval64, nf));
         EMIN_TRY(dalloc(c, &c->sgs_bval64, nb));
+        EMIN_TRY(dalloc(c, &c->sgs_bfval64, c->sgs_bnf));
+        EMIN_TRY(dalloc(c, &c->sgs_bbval64, c->sgs_bnb));
     }
     c->sgs_nf = nf;
     c->sgs_nb = nb;
     return sync(c);  // the host vectors must outlive the transfers
 }
 
-// the SGS values A^ at the plan's couplings, in the precision of T
+// the SGS values A^ at the plan's couplings (level and batched paths), in
+// the precision of T
 template <class T>
-void form_sgs_values(emin_ctx *c, T *fval, T *bval) {
-    if (c->opts.precond != EMIN_SGS || c->sgs_ngroups <= 0) return;
+void form_sgs_values(emin_ctx *c, T *fval, T *bval, T *bfval, T *bbval) {
+    if (c->opts.precond != EMIN_SGS) return;
     launch_sgs_values<T>(c->L, c->sgs_fown, c->sgs_fa, c->sgs_nf, c->sgs_bown, c->sgs_ba,
                          c->sgs_nb, c->Aj, c->Av, c->dsq, fval, bval);
+    launch_sgs_values<T>(c->L, c->sgs_bat_fown, c->sgs_bat_fa, c->sgs_bnf, c->sgs_bat_bown,
+                         c->sgs_bat_ba, c->sgs_bnb, c->Aj, c->Av, c->dsq, bfval, bbval);
 }
 
 // A^ and q in double (the FP64 path, or the adjoint of a mixed context)
@@ -341,7 +381,8 @@ void form_scaled64(emin_ctx *c) {
     else
         launch_scale_a<double>(c->L, c->n, c->Ap, c->Aj, c->Av, c->dsq, c->Ah64);
     if (c->k == 1) launch_qvec_k1<double>(c->L, c->n, c->Pp, c->Pj, c->Bc, c->qv64);
-    if (c->sgs_fval64) form_sgs_values<double>(c, c->sgs_fval64, c->sgs_bval64);
+    if (c->sgs_fval64) form_sgs_values<double>(c, c->sgs_fval64, c->sgs_bval64, c->sgs_bfval64,
+                                    c->sgs_bbval64);
     c->have64 = true;
 }
 
@@ -359,14 +400,16 @@ int run_setup(emin_ctx *c) {
             launch_to_float(L, c->Bc, c->Bc32, (long long)c->nc * c->k);
             launch_sell_values<float>(L, c->n, c->Ap, c->Aj, c->Av, c->dsq, c->sell_ptr, c->sa32,
                                       c->sw, c->spk32);
-            form_sgs_values<float>(c, c->sgs_fval32, c->sgs_bval32);
+            form_sgs_values<float>(c, c->sgs_fval32, c->sgs_bval32, c->sgs_bfval32,
+                                   c->sgs_bbval32);
             EMIN_TRY(start_pcg<float>(c, iter_ops32(c), c->w32, c->t32a));
         } else {
             launch_setup_k1<double>(L, c->n, c->dpos, c->Av, c->Pp, c->Pj, c->Bc, c->B, c->P0_in,
                                     c->opts.rank_policy, c->dint, c->dint + 2, c->dsq, c->dhalf,
                                     c->Ginv, c->qv64, c->P0, c->t64c);
             launch_sell_values<double>(L, c->n, c->Ap, c->Aj, c->Av, c->dsq, c->sell_ptr, c->sa64);
-            form_sgs_values<double>(c, c->sgs_fval64, c->sgs_bval64);
+            form_sgs_values<double>(c, c->sgs_fval64, c->sgs_bval64, c->sgs_bfval64,
+                                    c->sgs_bbval64);
             c->have64 = true;
             EMIN_TRY(start_pcg<double>(c, iter_ops64(c), c->w64, c->t64c));
         }
@@ -388,7 +431,8 @@ int run_setup(emin_ctx *c) {
         else
             launch_scale_a<float>(L, c->n, c->Ap, c->Aj, c->Av, c->dsq, c->Ah32);
         if (c->k == 1) launch_qvec_k1<float>(L, c->n, c->Pp, c->Pj, c->Bc, c->qv32);
-        form_sgs_values<float>(c, c->sgs_fval32, c->sgs_bval32);
+        form_sgs_values<float>(c, c->sgs_fval32, c->sgs_bval32, c->sgs_bfval32,
+                                   c->sgs_bbval32);
         launch_row_scale<double, float>(L, c->n, c->Pp, c->lanes, c->dhalf, 1.0, c->P0, c->t32a);
         EMIN_TRY(start_pcg<float>(c, iter_ops32(c), c->w32, c->t32a));
     } else {
@@ -1187,9 +1231,11 @@ int emin_backward(emin_ctx *c, const double *dL_dP, double *dL_dAval, double *dL
         if (!c->Ah64) EMIN_TRY(dalloc(c, &c->Ah64, c->nnz_a));
         if (c->sell_ptr && !c->sa64) EMIN_TRY(dalloc(c, &c->sa64, c->nnz_sell));
         if (c->k == 1 && !c->qv64) EMIN_TRY(dalloc(c, &c->qv64, c->nnz_p));
-        if (c->sgs_ngroups > 0 && !c->sgs_fval64) {
+        if (c->opts.precond == EMIN_SGS && !c->sgs_fval64) {
             EMIN_TRY(dalloc(c, &c->sgs_fval64, c->sgs_nf));
             EMIN_TRY(dalloc(c, &c->sgs_bval64, c->sgs_nb));
+            EMIN_TRY(dalloc(c, &c->sgs_bfval64, c->sgs_bnf));
+            EMIN_TRY(dalloc(c, &c->sgs_bbval64, c->sgs_bnb));
             c->have64 = false;
         }
     }

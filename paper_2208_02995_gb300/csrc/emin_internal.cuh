@@ -97,6 +97,14 @@ struct Work {
 // sweeps in group order.
 template <class T>
 struct SgsOps {
+    // batched path (see sgs.cu): class headers (8 ints: rows m, couplings
+    // nf / nb, forward pointer / index offsets, backward pointer / index
+    // offsets), batch headers (4 ints: class, lane-array offsets of the
+    // positions and of both sweeps' values), lane arrays interleaved by 32
+    int nbatch = 0, bmax_u = 0, bmax_v = 0;
+    const int *cls_hdr = nullptr, *bat_hdr = nullptr, *bat_rpos = nullptr;
+    const unsigned short *cls_ptr = nullptr, *cls_idx = nullptr;
+    const T *bat_fval = nullptr, *bat_bval = nullptr;
     int ngroups = 0;
     int cap = 0;                 // largest m * G
     int gmax = 0;                // largest G
@@ -238,10 +246,15 @@ int pk_blocks_per_sm(int double_precision);
 
 // projected block SGS (sgs.cu)
 struct SgsHost {
+    // level path (groups without enough structural twins)
     int ngroups = 0, cap = 0, gmax = 0;
     long long stage32 = 0, stage64 = 0;
     std::vector<int> hdr, rpos, fown, fa, bown, ba;
     std::vector<unsigned short> blob;
+    // batched path: classes of identical structure, batches of 32 groups
+    int nbatch = 0, bmax_u = 0, bmax_v = 0;
+    std::vector<int> cls_hdr, bat_hdr, bat_rpos, bat_fown, bat_fa, bat_bown, bat_ba;
+    std::vector<unsigned short> cls_ptr, cls_idx;
 };
 int build_sgs_plan(int n, int nc, const int *Ap, const int *Aj, const int *Pp, const int *Pj,
                    SgsHost &out);

@@ -20,6 +20,7 @@
 
 #include <algorithm>
 #include <thread>
+#include <unordered_map>
 #include <vector>
 
 #include "device_util.cuh"
@@ -30,6 +31,9 @@ namespace {
 
 constexpr int kSgsMaxCols = 8;        // columns per group
 constexpr int kSgsMaxRows = 65535;    // rows per group (16-bit local indices)
+constexpr int kBatchRows = 96;        // rows of a group swept by one lane (batched path)
+constexpr int kBatchMin = 8;          // groups of one structure before it is batched
+constexpr int kBatchCouplings = 256;  // couplings per sweep of a batched group
 
 inline int grid_for(long long work, int cap) {
     long long g = (work + kBlock - 1) / kBlock;
@@ -46,6 +50,10 @@ __global__ void k_sgs_values(long long nops, const int *__restrict__ own,
                              T *__restrict__ val) {
     for (long long o = blockIdx.x * (long long)blockDim.x + threadIdx.x; o < nops;
          o += (long long)gridDim.x * blockDim.x) {
+        if (own[o] < 0) {  // an empty lane of a batch
+            val[o] = T(0);
+            continue;
+        }
         const int e = aent[o];
         const double di = dsq[own[o]], a = Av[e], dl = dsq[Aj[e]];
         if constexpr (sizeof(T) == 4)
@@ -170,6 +178,83 @@ __global__ void k_sgs_sweep(int ngroups, const int *__restrict__ hdr, const int 
     }
 }
 
+// 16-byte asynchronous copies of `bytes` (a multiple of 16, both addresses
+// 16-byte aligned) from global to shared memory by the 32 lanes of a warp
+__device__ __forceinline__ void stage_async(void *dst, const void *src, int bytes, int lane) {
+    const unsigned base = (unsigned)__cvta_generic_to_shared(dst);
+    const char *s = static_cast<const char *>(src);
+    for (int q = lane; 16 * q < bytes; q += 32)
+        asm volatile("cp.async.cg.shared.global [%0], [%1], 16;\n" ::"r"(base + 16 * q),
+                     "l"(s + 16 * q)
+                     : "memory");
+    asm volatile("cp.async.commit_group;\n" ::: "memory");
+}
+__device__ __forceinline__ void async_wait_all() {
+    asm volatile("cp.async.wait_group 0;\n" ::: "memory");
+}
+
+// The batched sweep: 32 structurally identical groups of one column per
+// warp, one lane each.  The class structure (coupling pointers and local
+// indices, in row order) is the same for every lane and read as uniform
+// loads; each lane's u and coupling values sit in shared memory interleaved
+// by lane (row t of lane L at [32 t + L], conflict-free), the values of one
+// sweep at a time.  Each lane then sweeps its own block row by row, forward
+// and backward, with no synchronisation: no lane reads another lane's data.
+template <class T>
+__global__ void k_sgs_batch(int nbatch, const int *__restrict__ bat_hdr,
+                            const int *__restrict__ cls_hdr,
+                            const unsigned short *__restrict__ cls_ptr,
+                            const unsigned short *__restrict__ cls_idx,
+                            const int *__restrict__ rpos, const T *__restrict__ fval,
+                            const T *__restrict__ bval, const T *__restrict__ R,
+                            T *__restrict__ Z, const DevState *st, int umax, int vmax) {
+    if (st->stop) return;
+    extern __shared__ __align__(16) unsigned char sgs_smem[];
+    const int lane = threadIdx.x & 31;
+    T *u = reinterpret_cast<T *>(sgs_smem) + (size_t)(threadIdx.x >> 5) * 32 * (umax + vmax);
+    T *sv = u + 32 * umax;
+    const int nwarps = (gridDim.x * blockDim.x) >> 5;
+    for (int b = (blockIdx.x * blockDim.x + threadIdx.x) >> 5; b < nbatch; b += nwarps) {
+        const int *h = bat_hdr + 4 * (size_t)b;
+        const int *ch = cls_hdr + 8 * (size_t)h[0];
+        const int m = ch[0], nf = ch[1], nb = ch[2];
+        const unsigned short *fp = cls_ptr + ch[3], *fi = cls_idx + ch[4];
+        const unsigned short *bp = cls_ptr + ch[5], *bi = cls_idx + ch[6];
+        const int *rp = rpos + h[1];
+        // the forward values in flight (16-byte asynchronous copies), then
+        // the gather of r~, then one wait
+        stage_async(sv, fval + h[2], 32 * nf * (int)sizeof(T), lane);
+#pragma unroll 8
+        for (int t = 0; t < m; ++t) {
+            const int p = rp[32 * t + lane];
+            u[32 * t + lane] = p >= 0 ? R[p] : T(0);
+        }
+        async_wait_all();
+        __syncwarp();
+        for (int t = 0; t < m; ++t) {
+            T acc = u[32 * t + lane];
+            const int o1 = fp[t + 1];
+            for (int o = fp[t]; o < o1; ++o) acc = fmat(-sv[32 * o + lane], u[32 * fi[o] + lane], acc);
+            u[32 * t + lane] = acc;
+        }
+        __syncwarp();
+        stage_async(sv, bval + h[3], 32 * nb * (int)sizeof(T), lane);
+        async_wait_all();
+        __syncwarp();
+        for (int t = m - 1; t >= 0; --t) {
+            T acc = u[32 * t + lane];
+            const int o1 = bp[t + 1];
+            for (int o = bp[t]; o < o1; ++o) acc = fmat(-sv[32 * o + lane], u[32 * bi[o] + lane], acc);
+            u[32 * t + lane] = acc;
+        }
+        for (int t = 0; t < m; ++t) {
+            const int p = rp[32 * t + lane];
+            if (p >= 0) Z[p] = u[32 * t + lane];
+        }
+        __syncwarp();  // the buffers are refilled by the warp's next batch
+    }
+}
+
 // k = 1: z~ <- Pi z~ = z~ - q (q^T z~) per row and gamma = <r~, z~> in one
 // pass, then the scalar step of Algorithm 3 (gamma_0 or beta).
 template <class T>
@@ -284,50 +369,218 @@ int build_sgs_plan(int n, int nc, const int *Ap, const int *Aj, const int *Pp, c
     unsigned nth = std::thread::hardware_concurrency();
     nth = std::max(1u, std::min(nth, 32u));
     if (ng < 1024) nth = 1;
+    auto run = [&](auto &&fn) {
+        if (nth == 1) {
+            fn(0);
+        } else {
+            std::vector<std::thread> th;
+            for (unsigned t = 0; t < nth; ++t) th.emplace_back(fn, (int)t);
+            for (auto &t : th) t.join();
+        }
+    };
+    // the couplings of group g inside its block (local indices, A entries)
+    struct Lists {
+        std::vector<int> rows;
+        std::vector<std::vector<int>> lo, lo_e, up, up_e;
+        long long nf = 0, nb = 0;
+    };
+    auto lists = [&](int g, std::vector<int> &loc, Lists &L) {
+        const int j = gcol[g], m = colp[j + 1] - colp[j];
+        L.rows.assign(crow.begin() + colp[j], crow.begin() + colp[j + 1]);
+        L.lo.assign(m, {});
+        L.lo_e.assign(m, {});
+        L.up.assign(m, {});
+        L.up_e.assign(m, {});
+        L.nf = L.nb = 0;
+        for (int t = 0; t < m; ++t) loc[L.rows[t]] = t;
+        for (int t = 0; t < m; ++t) {
+            const int i = L.rows[t];
+            for (int e = Ap[i]; e < Ap[i + 1]; ++e) {
+                const int l = Aj[e];
+                if (l == i || l < 0 || l >= n) continue;
+                const int tl = loc[l];
+                if (tl < 0) continue;
+                if (tl < t) {
+                    L.lo[t].push_back(tl);
+                    L.lo_e[t].push_back(e);
+                    ++L.nf;
+                } else {
+                    L.up[t].push_back(tl);
+                    L.up_e[t].push_back(e);
+                    ++L.nb;
+                }
+            }
+        }
+        for (int t = 0; t < m; ++t) loc[L.rows[t]] = -1;
+    };
+    // phase 1: a structure hash of every group that could be batched (one
+    // column, at most kBatchRows rows)
+    std::vector<unsigned long long> ghash(ng, 0);
+    std::vector<char> gelig(ng, 0);
+    run([&](int tid) {
+        const int g0 = (int)((long long)ng * tid / nth), g1 = (int)((long long)ng * (tid + 1) / nth);
+        std::vector<int> loc(n, -1);
+        Lists L;
+        for (int g = g0; g < g1; ++g) {
+            const int m = colp[gcol[g] + 1] - colp[gcol[g]];
+            if (gsize[g] != 1 || m > kBatchRows) continue;
+            lists(g, loc, L);
+            if (L.nf > kBatchCouplings || L.nb > kBatchCouplings) continue;
+            unsigned long long h = 1469598103934665603ULL;
+            auto mix = [&](unsigned long long v) { h = (h ^ v) * 1099511628211ULL; };
+            mix((unsigned long long)m);
+            for (int t = 0; t < m; ++t) {
+                mix(0x100000000ULL + L.lo[t].size());
+                for (int v : L.lo[t]) mix((unsigned long long)v);
+                mix(0x200000000ULL + L.up[t].size());
+                for (int v : L.up[t]) mix((unsigned long long)v);
+            }
+            ghash[g] = h;
+            gelig[g] = 1;
+        }
+    });
+    // phase 2: classes of structurally identical groups; a class with at
+    // least kBatchMin members is swept in batches of 32 (one lane a group)
+    out = SgsHost();
+    std::unordered_map<unsigned long long, int> cls_of_hash;
+    std::vector<int> gcls(ng, -1), cls_rep, cls_count;
+    for (int g = 0; g < ng; ++g) {
+        if (!gelig[g]) continue;
+        auto it = cls_of_hash.find(ghash[g]);
+        int c;
+        if (it == cls_of_hash.end()) {
+            c = (int)cls_rep.size();
+            cls_of_hash.emplace(ghash[g], c);
+            cls_rep.push_back(g);
+            cls_count.push_back(0);
+        } else {
+            c = it->second;
+        }
+        gcls[g] = c;
+        cls_count[c]++;
+    }
+    std::vector<int> bcls(cls_rep.size(), -1);  // class -> batched class index
+    std::vector<Lists> canon;
+    std::vector<int> gbatch(ng, -1), glane(ng, -1);
+    {
+        std::vector<int> loc(n, -1);
+        std::vector<int> next(cls_rep.size(), 0);
+        for (size_t c = 0; c < cls_rep.size(); ++c) {
+            if (cls_count[c] < kBatchMin) continue;
+            bcls[c] = (int)canon.size();
+            canon.emplace_back();
+            lists(cls_rep[c], loc, canon.back());
+        }
+        // batches in group order within each class
+        std::vector<int> cls_first_batch(canon.size(), 0);
+        int nb_total = 0;
+        for (size_t c = 0; c < cls_rep.size(); ++c)
+            if (bcls[c] >= 0) {
+                cls_first_batch[bcls[c]] = nb_total;
+                nb_total += (cls_count[c] + 31) / 32;
+            }
+        for (int g = 0; g < ng; ++g) {
+            const int c = gcls[g];
+            if (c < 0 || bcls[c] < 0) continue;
+            const int k = next[c]++;
+            gbatch[g] = cls_first_batch[bcls[c]] + k / 32;
+            glane[g] = k % 32;
+        }
+        // class structure: coupling pointers and local indices of both sweeps
+        for (size_t b = 0; b < canon.size(); ++b) {
+            const Lists &L = canon[b];
+            const int m = (int)L.rows.size();
+            const int h[8] = {m, (int)L.nf, (int)L.nb, (int)out.cls_ptr.size(), 0, 0, 0, 0};
+            out.cls_hdr.insert(out.cls_hdr.end(), h, h + 8);
+            int cp0 = (int)out.cls_ptr.size();
+            out.cls_hdr[8 * b + 3] = cp0;
+            out.cls_hdr[8 * b + 4] = (int)out.cls_idx.size();
+            int o = 0;
+            for (int t = 0; t < m; ++t) {
+                out.cls_ptr.push_back((unsigned short)o);
+                for (int v : L.lo[t]) out.cls_idx.push_back((unsigned short)v), ++o;
+            }
+            out.cls_ptr.push_back((unsigned short)o);
+            out.cls_hdr[8 * b + 5] = (int)out.cls_ptr.size();
+            out.cls_hdr[8 * b + 6] = (int)out.cls_idx.size();
+            o = 0;
+            for (int t = 0; t < m; ++t) {
+                out.cls_ptr.push_back((unsigned short)o);
+                for (int v : L.up[t]) out.cls_idx.push_back((unsigned short)v), ++o;
+            }
+            out.cls_ptr.push_back((unsigned short)o);
+            out.bmax_u = std::max(out.bmax_u, m);
+            out.bmax_v = std::max(out.bmax_v, (int)std::max(L.nf, L.nb));
+        }
+        // batch headers and the lane arrays (empty lanes: position -1)
+        long long rp = 0, fv = 0, bv = 0;
+        for (size_t c = 0; c < cls_rep.size(); ++c) {
+            if (bcls[c] < 0) continue;
+            const Lists &L = canon[bcls[c]];
+            const int nbat = (cls_count[c] + 31) / 32;
+            for (int k = 0; k < nbat; ++k) {
+                const int h[4] = {bcls[c], (int)rp, (int)fv, (int)bv};
+                out.bat_hdr.insert(out.bat_hdr.end(), h, h + 4);
+                rp += 32LL * (long long)L.rows.size();
+                fv += 32LL * L.nf;
+                bv += 32LL * L.nb;
+            }
+        }
+        if (rp > 0x7fffffffLL || fv > 0x7fffffffLL || bv > 0x7fffffffLL) return EMIN_ERR_ARG;
+        out.nbatch = (int)(out.bat_hdr.size() / 4);
+        out.bat_rpos.assign(rp, -1);
+        out.bat_fown.assign(fv, -1);
+        out.bat_fa.assign(fv, 0);
+        out.bat_bown.assign(bv, -1);
+        out.bat_ba.assign(bv, 0);
+    }
+    // phase 3: batched groups fill their lane (after checking their lists
+    // against the class's, so that equal hashes never stand in for equal
+    // structure); the other groups get a level plan
     std::vector<GroupOut> part(nth);
     std::vector<int> bad(nth, 0);
-    auto work = [&](int tid) {
+    run([&](int tid) {
         GroupOut &o = part[tid];
         const int g0 = (int)((long long)ng * tid / nth), g1 = (int)((long long)ng * (tid + 1) / nth);
         std::vector<int> loc(n, -1);
+        Lists L;
         for (int g = g0; g < g1 && !bad[tid]; ++g) {
             const int j = gcol[g], G = gsize[g], m = colp[j + 1] - colp[j];
-            std::vector<int> rows(crow.begin() + colp[j], crow.begin() + colp[j + 1]);
-            for (int t = 0; t < m; ++t) loc[rows[t]] = t;
-            std::vector<std::vector<int>> lo(m), lo_e(m), up(m), up_e(m);
-            long long nf = 0, nb = 0;
-            for (int t = 0; t < m; ++t) {
-                const int i = rows[t];
-                for (int e = Ap[i]; e < Ap[i + 1]; ++e) {
-                    const int l = Aj[e];
-                    if (l == i || l < 0 || l >= n) continue;
-                    const int tl = loc[l];
-                    if (tl < 0) continue;
-                    if (tl < t) {
-                        lo[t].push_back(tl);
-                        lo_e[t].push_back(e);
-                        ++nf;
-                    } else {
-                        up[t].push_back(tl);
-                        up_e[t].push_back(e);
-                        ++nb;
-                    }
+            lists(g, loc, L);
+            if (gbatch[g] >= 0) {
+                const Lists &C = canon[bcls[gcls[g]]];
+                if (C.lo == L.lo && C.up == L.up) {
+                    const int *h = &out.bat_hdr[4 * (size_t)gbatch[g]];
+                    const int lane = glane[g];
+                    for (int t = 0; t < m; ++t) out.bat_rpos[h[1] + 32LL * t + lane] = cpos[colp[j] + t];
+                    long long q = 0;
+                    for (int t = 0; t < m; ++t)
+                        for (size_t x = 0; x < L.lo[t].size(); ++x, ++q) {
+                            out.bat_fown[h[2] + 32 * q + lane] = L.rows[t];
+                            out.bat_fa[h[2] + 32 * q + lane] = L.lo_e[t][x];
+                        }
+                    q = 0;
+                    for (int t = 0; t < m; ++t)
+                        for (size_t x = 0; x < L.up[t].size(); ++x, ++q) {
+                            out.bat_bown[h[3] + 32 * q + lane] = L.rows[t];
+                            out.bat_ba[h[3] + 32 * q + lane] = L.up_e[t][x];
+                        }
+                    continue;
                 }
             }
-            for (int t = 0; t < m; ++t) loc[rows[t]] = -1;
-            if (nf > 65535 || nb > 65535) {  // 16-bit coupling pointers
+            if (L.nf > 65535 || L.nb > 65535) {  // 16-bit coupling pointers
                 bad[tid] = 1;
                 break;
             }
             std::vector<int> fl(m, 0), bl(m, 0);
             for (int t = 0; t < m; ++t)
-                for (int tl : lo[t]) fl[t] = std::max(fl[t], fl[tl] + 1);
+                for (int tl : L.lo[t]) fl[t] = std::max(fl[t], fl[tl] + 1);
             for (int t = m - 1; t >= 0; --t)
-                for (int tu : up[t]) bl[t] = std::max(bl[t], bl[tu] + 1);
+                for (int tu : L.up[t]) bl[t] = std::max(bl[t], bl[tu] + 1);
             std::vector<unsigned short> flvl, frow, foptr, fidx, blvl, brow, boptr, bidx;
             const int fo0 = (int)o.fa.size(), bo0 = (int)o.ba.size();
-            emit_sweep(fl, lo, lo_e, rows, flvl, frow, foptr, fidx, o.fown, o.fa);
-            emit_sweep(bl, up, up_e, rows, blvl, brow, boptr, bidx, o.bown, o.ba);
+            emit_sweep(fl, L.lo, L.lo_e, L.rows, flvl, frow, foptr, fidx, o.fown, o.fa);
+            emit_sweep(bl, L.up, L.up_e, L.rows, blvl, brow, boptr, bidx, o.bown, o.ba);
             const int b0 = (int)o.blob.size();
             for (auto *v : {&flvl, &frow, &foptr, &blvl, &brow, &boptr, &fidx, &bidx})
                 o.blob.insert(o.blob.end(), v->begin(), v->end());
@@ -335,22 +588,14 @@ int build_sgs_plan(int n, int nc, const int *Ap, const int *Aj, const int *Pp, c
             const int r0 = (int)o.rpos.size();
             for (int t = 0; t < m; ++t) o.rpos.push_back(cpos[colp[j] + t]);
             const int h[kHdr] = {m, G, r0, b0 / 8, (int)(o.blob.size() - b0) / 8, fo0, bo0,
-                                 (int)nf, (int)nb, (int)flvl.size() - 1, (int)blvl.size() - 1, j};
+                                 (int)L.nf, (int)L.nb, (int)flvl.size() - 1,
+                                 (int)blvl.size() - 1, j};
             o.hdr.insert(o.hdr.end(), h, h + kHdr);
         }
-    };
-    if (nth == 1) {
-        work(0);
-    } else {
-        std::vector<std::thread> th;
-        for (unsigned t = 0; t < nth; ++t) th.emplace_back(work, (int)t);
-        for (auto &t : th) t.join();
-    }
+    });
     for (unsigned t = 0; t < nth; ++t)
         if (bad[t]) return EMIN_ERR_ARG;
-    // concatenate the parts, shifting their row, blob and coupling offsets
-    out = SgsHost();
-    out.ngroups = ng;
+    // concatenate the level-plan parts, shifting their offsets
     long long row_off = 0, blob_off = 0, fo_off = 0, bo_off = 0;
     for (unsigned t = 0; t < nth; ++t) {
         GroupOut &o = part[t];
@@ -368,7 +613,6 @@ int build_sgs_plan(int n, int nc, const int *Ap, const int *Aj, const int *Pp, c
             h[6] += (int)bo_off;
             out.cap = std::max(out.cap, h[0] * h[1]);
             out.gmax = std::max(out.gmax, h[1]);
-            // bytes of u + blob + values (float / double) if staged
             const long long ub = ((long long)h[0] * h[1] * 4 + 15) / 16 * 16;
             out.stage32 = std::max(out.stage32, ub + 16LL * h[4] + 4LL * (h[7] + h[8]));
             const long long ub8 = ((long long)h[0] * h[1] * 8 + 15) / 16 * 16;
@@ -387,6 +631,7 @@ int build_sgs_plan(int n, int nc, const int *Ap, const int *Aj, const int *Pp, c
         bo_off += (long long)o.ba.size();
         o = GroupOut();
     }
+    out.ngroups = (int)(out.hdr.size() / kHdr);
     return EMIN_OK;
 }
 
@@ -445,14 +690,43 @@ void sweep_with(const Launch &L, const SgsOps<T> &s, const T *R, T *Z, const Dev
 // coupling counts make the two halves diverge.)
 template <class T>
 void launch_sgs_sweep(const Launch &L, const SgsOps<T> &s, const T *R, T *Z, const DevState *st) {
-    if (s.ngroups <= 0) return;
-    const long long ubytes = ((long long)s.cap * sizeof(T) + 15) / 16 * 16;
-    const long long slot = std::max(ubytes, (long long)(sizeof(T) == 4 ? 4096 : 8192));
-    if (s.gmax <= 1)
-        sweep_with<T, 1, 32>(L, s, R, Z, st, slot);
-    else
-        sweep_with<T, kSgsMaxCols, 32>(L, s, R, Z, st, slot);
-    note_launch();
+    if (s.nbatch > 0) {
+        // u and one sweep's values of 32 lanes per warp
+        const long long per_warp = 32LL * (s.bmax_u + s.bmax_v) * sizeof(T);
+        static bool attr = false;
+        if (!attr) {
+            cudaFuncSetAttribute(k_sgs_batch<T>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                 200 * 1024);
+            cudaGetLastError();
+            attr = true;
+        }
+        long long wpb = (96 * 1024) / per_warp;
+        wpb = std::max(1LL, std::min(8LL, wpb));
+        const int threads = (int)(32 * wpb);
+        const size_t smem = (size_t)(wpb * per_warp);
+        int per_sm = 1;
+        if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_sgs_batch<T>, threads, smem) !=
+                cudaSuccess ||
+            per_sm < 1) {
+            cudaGetLastError();
+            per_sm = 1;
+        }
+        long long blocks = ((long long)s.nbatch + wpb - 1) / wpb;
+        blocks = std::min(blocks, (long long)L.nsm * per_sm);
+        k_sgs_batch<T><<<(int)blocks, threads, smem, L.stream>>>(
+            s.nbatch, s.bat_hdr, s.cls_hdr, s.cls_ptr, s.cls_idx, s.bat_rpos, s.bat_fval,
+            s.bat_bval, R, Z, st, s.bmax_u, s.bmax_v);
+        note_launch();
+    }
+    if (s.ngroups > 0) {
+        const long long ubytes = ((long long)s.cap * sizeof(T) + 15) / 16 * 16;
+        const long long slot = std::max(ubytes, (long long)(sizeof(T) == 4 ? 4096 : 8192));
+        if (s.gmax <= 1)
+            sweep_with<T, 1, 32>(L, s, R, Z, st, slot);
+        else
+            sweep_with<T, kSgsMaxCols, 32>(L, s, R, Z, st, slot);
+        note_launch();
+    }
 }
 
 // k = 1: projection and gamma in one pass; otherwise projection, then gamma
