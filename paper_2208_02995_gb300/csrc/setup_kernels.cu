@@ -286,6 +286,91 @@ __global__ void k_restore(int n, const int *__restrict__ Pp, const int *__restri
 //     p += b G^{-1} (B_i - b^T p);
 //   the iteration's start vector x0 = D^{1/2} p in the iteration type.
 // ---------------------------------------------------------------------------
+// One row of the fused k = 1 set-up with at most M entries (M >= the row's m).
+template <class Tit, int M>
+__device__ __forceinline__ void setup_row_k1(int i, const int *__restrict__ dpos,
+                                             const double *__restrict__ Av,
+                                             const int *__restrict__ Pp,
+                                             const int *__restrict__ Pj,
+                                             const double *__restrict__ Bc,
+                                             const double *__restrict__ B,
+                                             const double *__restrict__ P0_in, int policy,
+                                             int *flags, int *ndef, double *dsq, double *dhalf,
+                                             double *Ginv, Tit *qv, double *P0, Tit *x0) {
+    const int p0 = Pp[i], m = Pp[i + 1] - p0;
+    double b[M], p[M];
+#pragma unroll
+    for (int s = 0; s < M; ++s) {
+        const bool h = s < m;
+        b[s] = h ? Bc[Pj[p0 + s]] : 0.0;
+        p[s] = h ? P0_in[p0 + s] : 0.0;
+    }
+    const double Bi = B[i];
+    const int dp = dpos[i];
+    double d = (dp >= 0) ? Av[dp] : 0.0;
+    if (!(d > 0.0) || !isfinite(d)) {
+        atomicOr(flags, F_DIAG);
+        d = 1.0;
+    }
+    // the scaling is a change of variables of the iteration: the float
+    // path takes it in float (exactly representable in double, so every
+    // later use sees the same value), the FP64 path in double
+    double sq, dh;
+    if constexpr (sizeof(Tit) == 4) {
+        const float df = (float)d;
+        const float sf = (df > 0.f && isfinite(df)) ? rsqrtf(df) : 1.f;
+        if (!(df > 0.f) || !isfinite(df)) atomicOr(flags, F_DIAG);
+        sq = (double)sf;
+        dh = (double)(df * sf);
+    } else {
+        sq = rsqrt_newton(d);
+        dh = d * sq;
+    }
+    dsq[i] = sq;
+    dhalf[i] = dh;
+    double G = 0.0;
+#pragma unroll
+    for (int s = 0; s < M; ++s) G = fma(b[s], b[s], G);
+    double r = 0.0, gi = 0.0;
+    if (sizeof(Tit) == 4 && G >= 1e-30 && G <= 1e30) {
+        // float path: q = b / |b| is stored in float, so 1/|b| is taken in
+        // float; 1/G (for the least-norm correction and the final FP64
+        // restore) by two Newton-Raphson steps for the reciprocal,
+        // x <- x + x (1 - G x), from the float seed 1/|b|^2, each step
+        // squaring the relative error (about 1e-7 -> 1e-14 -> 1e-28)
+        const float rf = rsqrtf((float)G);
+        r = (double)rf;
+        gi = (double)(rf * rf);
+        gi = fma(gi, fma(-G, gi, 1.0), gi);
+        gi = fma(gi, fma(-G, gi, 1.0), gi);
+    } else if (G > 0.0) {
+        r = rsqrt_newton(G);
+        gi = r * r;
+    } else if (policy == EMIN_RANK_PINV) {
+        atomicAdd(ndef, 1);
+    } else {
+        atomicOr(flags, F_RANK);
+    }
+    Ginv[i] = gi;
+    double res = Bi;
+#pragma unroll
+    for (int s = 0; s < M; ++s) res = fma(-b[s], p[s], res);
+    const double c = gi * res;
+#pragma unroll
+    for (int s = 0; s < M; ++s)
+        if (s < m) {
+            const double pc = fma(b[s], c, p[s]);
+            P0[p0 + s] = pc;
+            if constexpr (sizeof(Tit) == 4) {
+                x0[p0 + s] = (float)dh * (float)pc;
+                qv[p0 + s] = (float)b[s] * (float)r;
+            } else {
+                x0[p0 + s] = dh * pc;
+                qv[p0 + s] = b[s] * r;
+            }
+        }
+}
+
 template <class Tit>
 __global__ void k_setup_k1(int n, const int *__restrict__ dpos, const double *__restrict__ Av,
                            const int *__restrict__ Pp, const int *__restrict__ Pj,
@@ -293,112 +378,96 @@ __global__ void k_setup_k1(int n, const int *__restrict__ dpos, const double *__
                            const double *__restrict__ P0_in, int policy, int *flags, int *ndef,
                            double *dsq, double *dhalf, double *Ginv, Tit *qv, double *P0,
                            Tit *x0) {
-    for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < n; i += gridDim.x * blockDim.x) {
-        const int p0 = Pp[i], m = Pp[i + 1] - p0;
-        double b[4], p[4];
-#pragma unroll
-        for (int s = 0; s < 4; ++s) {
-            const bool h = s < m;
-            b[s] = h ? Bc[Pj[p0 + s]] : 0.0;
-            p[s] = h ? P0_in[p0 + s] : 0.0;
+    // rows in warp-uniform passes, so that each warp runs the body for the
+    // largest row of P among its 32 rows (no FP64 work on absent slots)
+    const int lane = threadIdx.x & 31;
+    const int nwarps = (gridDim.x * blockDim.x) >> 5;
+    for (int base = ((blockIdx.x * blockDim.x + threadIdx.x) >> 5) * 32; base < n;
+         base += nwarps * 32) {
+        const int i = base + lane;
+        const bool row = i < n;
+        const int m = row ? Pp[i + 1] - Pp[i] : 0;
+        const unsigned mw = __reduce_max_sync(0xffffffffu, (unsigned)m);
+        if (!row) continue;
+        switch (mw) {
+            case 0:
+            case 1:
+                setup_row_k1<Tit, 1>(i, dpos, Av, Pp, Pj, Bc, B, P0_in, policy, flags, ndef, dsq,
+                                     dhalf, Ginv, qv, P0, x0);
+                break;
+            case 2:
+                setup_row_k1<Tit, 2>(i, dpos, Av, Pp, Pj, Bc, B, P0_in, policy, flags, ndef, dsq,
+                                     dhalf, Ginv, qv, P0, x0);
+                break;
+            case 3:
+                setup_row_k1<Tit, 3>(i, dpos, Av, Pp, Pj, Bc, B, P0_in, policy, flags, ndef, dsq,
+                                     dhalf, Ginv, qv, P0, x0);
+                break;
+            default:
+                setup_row_k1<Tit, 4>(i, dpos, Av, Pp, Pj, Bc, B, P0_in, policy, flags, ndef, dsq,
+                                     dhalf, Ginv, qv, P0, x0);
         }
-        const double Bi = B[i];
-        const int dp = dpos[i];
-        double d = (dp >= 0) ? Av[dp] : 0.0;
-        if (!(d > 0.0) || !isfinite(d)) {
-            atomicOr(flags, F_DIAG);
-            d = 1.0;
-        }
-        // the scaling is a change of variables of the iteration: the float
-        // path takes it in float (exactly representable in double, so every
-        // later use sees the same value), the FP64 path in double
-        double sq, dh;
-        if constexpr (sizeof(Tit) == 4) {
-            const float df = (float)d;
-            const float sf = (df > 0.f && isfinite(df)) ? rsqrtf(df) : 1.f;
-            if (!(df > 0.f) || !isfinite(df)) atomicOr(flags, F_DIAG);
-            sq = (double)sf;
-            dh = (double)(df * sf);
-        } else {
-            sq = rsqrt_newton(d);
-            dh = d * sq;
-        }
-        dsq[i] = sq;
-        dhalf[i] = dh;
-        double G = 0.0;
-#pragma unroll
-        for (int s = 0; s < 4; ++s) G = fma(b[s], b[s], G);
-        double r = 0.0, gi = 0.0;
-        if (sizeof(Tit) == 4 && G >= 1e-30 && G <= 1e30) {
-            // float path: q = b / |b| is stored in float, so 1/|b| is taken in
-            // float; 1/G (for the least-norm correction and the final FP64
-            // restore) by two Newton-Raphson steps for the reciprocal,
-            // x <- x + x (1 - G x), from the float seed 1/|b|^2, each step
-            // squaring the relative error (about 1e-7 -> 1e-14 -> 1e-28)
-            const float rf = rsqrtf((float)G);
-            r = (double)rf;
-            gi = (double)(rf * rf);
-            gi = fma(gi, fma(-G, gi, 1.0), gi);
-            gi = fma(gi, fma(-G, gi, 1.0), gi);
-        } else if (G > 0.0) {
-            r = rsqrt_newton(G);
-            gi = r * r;
-        } else if (policy == EMIN_RANK_PINV) {
-            atomicAdd(ndef, 1);
-        } else {
-            atomicOr(flags, F_RANK);
-        }
-        Ginv[i] = gi;
-        double res = Bi;
-#pragma unroll
-        for (int s = 0; s < 4; ++s) res = fma(-b[s], p[s], res);
-        const double c = gi * res;
-#pragma unroll
-        for (int s = 0; s < 4; ++s)
-            if (s < m) {
-                const double pc = fma(b[s], c, p[s]);
-                P0[p0 + s] = pc;
-                if constexpr (sizeof(Tit) == 4) {
-                    x0[p0 + s] = (float)dh * (float)pc;
-                    qv[p0 + s] = (float)b[s] * (float)r;
-                } else {
-                    x0[p0 + s] = dh * pc;
-                    qv[p0 + s] = b[s] * r;
-                }
-            }
     }
 }
 
 // Final prolongation for k = 1 (rows of P with at most 4 entries):
 // p = P0 + D^{-1/2} dW~ and, when `correct`, the least-norm constraint
 // correction in double p += b G^{-1} (B_i - b^T p) (b = Bc(J_i)).
+// One row of the k = 1 final P with at most M entries (M >= the row's m).
+template <class Tx, int M>
+__device__ __forceinline__ void final_row_k1(int i, const int *__restrict__ Pp,
+                                             const int *__restrict__ Pj,
+                                             const double *__restrict__ Bc,
+                                             const double *__restrict__ Ginv,
+                                             const double *__restrict__ P0,
+                                             const Tx *__restrict__ X,
+                                             const double *__restrict__ dsq,
+                                             const double *__restrict__ B, int correct,
+                                             double *__restrict__ P) {
+    const int p0 = Pp[i], m = Pp[i + 1] - p0;
+    const double f = dsq[i];
+    double p[M], b[M];
+#pragma unroll
+    for (int s = 0; s < M; ++s) {
+        const bool h = s < m;
+        p[s] = h ? fma(f, (double)X[p0 + s], P0[p0 + s]) : 0.0;
+        b[s] = (h && correct) ? Bc[Pj[p0 + s]] : 0.0;
+    }
+    if (correct) {
+        double r = B[i];
+#pragma unroll
+        for (int s = 0; s < M; ++s) r = fma(-b[s], p[s], r);
+        const double c = Ginv[i] * r;
+#pragma unroll
+        for (int s = 0; s < M; ++s) p[s] = fma(b[s], c, p[s]);
+    }
+#pragma unroll
+    for (int s = 0; s < M; ++s)
+        if (s < m) P[p0 + s] = p[s];
+}
+
 template <class Tx>
 __global__ void k_final_k1(int n, const int *__restrict__ Pp, const int *__restrict__ Pj,
                            const double *__restrict__ Bc, const double *__restrict__ Ginv,
                            const double *__restrict__ P0, const Tx *__restrict__ X,
                            const double *__restrict__ dsq, const double *__restrict__ B,
                            int correct, double *__restrict__ P) {
-    for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < n; i += gridDim.x * blockDim.x) {
-        const int p0 = Pp[i], m = Pp[i + 1] - p0;
-        const double f = dsq[i];
-        double p[4], b[4];
-#pragma unroll
-        for (int s = 0; s < 4; ++s) {
-            const bool h = s < m;
-            p[s] = h ? fma(f, (double)X[p0 + s], P0[p0 + s]) : 0.0;
-            b[s] = (h && correct) ? Bc[Pj[p0 + s]] : 0.0;
+    const int lane = threadIdx.x & 31;
+    const int nwarps = (gridDim.x * blockDim.x) >> 5;
+    for (int base = ((blockIdx.x * blockDim.x + threadIdx.x) >> 5) * 32; base < n;
+         base += nwarps * 32) {
+        const int i = base + lane;
+        const bool row = i < n;
+        const int m = row ? Pp[i + 1] - Pp[i] : 0;
+        const unsigned mw = __reduce_max_sync(0xffffffffu, (unsigned)m);
+        if (!row) continue;
+        switch (mw) {
+            case 0:
+            case 1: final_row_k1<Tx, 1>(i, Pp, Pj, Bc, Ginv, P0, X, dsq, B, correct, P); break;
+            case 2: final_row_k1<Tx, 2>(i, Pp, Pj, Bc, Ginv, P0, X, dsq, B, correct, P); break;
+            case 3: final_row_k1<Tx, 3>(i, Pp, Pj, Bc, Ginv, P0, X, dsq, B, correct, P); break;
+            default: final_row_k1<Tx, 4>(i, Pp, Pj, Bc, Ginv, P0, X, dsq, B, correct, P);
         }
-        if (correct) {
-            double r = B[i];
-#pragma unroll
-            for (int s = 0; s < 4; ++s) r = fma(-b[s], p[s], r);
-            const double c = Ginv[i] * r;
-#pragma unroll
-            for (int s = 0; s < 4; ++s) p[s] = fma(b[s], c, p[s]);
-        }
-#pragma unroll
-        for (int s = 0; s < 4; ++s)
-            if (s < m) P[p0 + s] = p[s];
     }
 }
 
