@@ -256,8 +256,18 @@ const char *emin_strerror(int status);
  * call of this thread. */
 const char *emin_last_error(void);
 
-/* Release every resource of the context (NULL is accepted). */
+/* Release every resource of the context (NULL is accepted).  The device
+ * memory of a context comes from a stream-ordered pool per device that the
+ * library owns and that keeps freed memory for the next context (so that
+ * creating and destroying contexts of similar sizes maps no new pages and
+ * does not synchronise the device); destroy frees it on the context's
+ * stream after waiting for that stream's work. */
 void emin_destroy(emin_ctx *ctx);
+
+/* Return the device memory cached in the library's pools (what destroyed
+ * contexts released) to the driver; the memory of live contexts stays.
+ * EMIN_OK, or EMIN_ERR_CUDA if the driver refused. */
+int emin_trim_memory(void);
 
 #ifdef __cplusplus
 }

@@ -9,6 +9,7 @@
 #include <atomic>
 #include <cstdio>
 #include <cstring>
+#include <mutex>
 #include <new>
 #include <vector>
 
@@ -86,6 +87,8 @@ struct emin_ctx {
     int *hint = nullptr;         // pinned mirror of dint
     int applied_seen = 0;
     std::vector<void *> dev_allocs;
+    cudaMemPool_t pool = nullptr;  // stream-ordered pool of dev_allocs (null: cudaMalloc)
+    void *host_blk = nullptr;      // pinned block holding hstate and hint
     // instrumentation
     int timing = 0;  // 0 off, else time the masked product of every timing-th iteration
     std::vector<cudaEvent_t> events;  // start/stop pairs, one per timed launch
@@ -117,15 +120,85 @@ struct DeviceGuard {
     }
 };
 
+// Device memory of every context comes from one stream-ordered pool per
+// device that keeps what is freed (release threshold: unlimited): a context
+// created after another of similar size maps no new pages, and a destroyed
+// context returns its memory without a device-wide synchronisation.
+// emin_trim_memory() gives the cached memory back to the driver.
+constexpr int kMaxDevices = 64;
+std::mutex g_pool_mutex;
+cudaMemPool_t g_pools[kMaxDevices] = {};
+std::vector<void *> g_host_blocks;  // recycled pinned blocks (kHostBlock bytes)
+constexpr size_t kHostBlock = 256;
+constexpr size_t kHintOffset = 128;
+static_assert(sizeof(DevState) <= kHintOffset, "state mirror overlaps the flag mirror");
+
+cudaMemPool_t device_pool(int dev) {
+    if (dev < 0 || dev >= kMaxDevices) return nullptr;
+    std::lock_guard<std::mutex> lk(g_pool_mutex);
+    if (!g_pools[dev]) {
+        int supported = 0;
+        if (cudaDeviceGetAttribute(&supported, cudaDevAttrMemoryPoolsSupported, dev) !=
+                cudaSuccess ||
+            !supported) {
+            cudaGetLastError();
+            return nullptr;
+        }
+        cudaMemPoolProps props = {};
+        props.allocType = cudaMemAllocationTypePinned;
+        props.handleTypes = cudaMemHandleTypeNone;
+        props.location.type = cudaMemLocationTypeDevice;
+        props.location.id = dev;
+        cudaMemPool_t pool = nullptr;
+        if (cudaMemPoolCreate(&pool, &props) != cudaSuccess) {
+            cudaGetLastError();
+            return nullptr;
+        }
+        unsigned long long keep = ~0ull;
+        cudaMemPoolSetAttribute(pool, cudaMemPoolAttrReleaseThreshold, &keep);
+        g_pools[dev] = pool;
+    }
+    return g_pools[dev];
+}
+
+void *host_block_get() {
+    {
+        std::lock_guard<std::mutex> lk(g_pool_mutex);
+        if (!g_host_blocks.empty()) {
+            void *b = g_host_blocks.back();
+            g_host_blocks.pop_back();
+            return b;
+        }
+    }
+    void *b = nullptr;
+    if (cudaMallocHost(&b, kHostBlock) != cudaSuccess) {
+        cudaGetLastError();
+        return nullptr;
+    }
+    return b;
+}
+
+void host_block_put(void *b) {
+    if (!b) return;
+    std::lock_guard<std::mutex> lk(g_pool_mutex);
+    g_host_blocks.push_back(b);
+}
+
+void release_dev(emin_ctx *c, void *p) {
+    if (c->pool) cudaFreeAsync(p, c->stream);
+    else cudaFree(p);
+}
+
 template <class T>
 int dalloc(emin_ctx *c, T **p, long long count) {
     size_t bytes = (size_t)(count > 0 ? count : 1) * sizeof(T);
     bytes = (bytes + 255) & ~(size_t)255;
     void *q = nullptr;
-    const cudaError_t e = cudaMalloc(&q, bytes);
+    const cudaError_t e =
+        c->pool ? cudaMallocFromPoolAsync(&q, bytes, c->pool, c->stream) : cudaMalloc(&q, bytes);
     if (e != cudaSuccess) {
-        std::snprintf(g_last_error, sizeof(g_last_error), "cudaMalloc(%zu): %s", bytes,
-                      cudaGetErrorName(e));
+        std::snprintf(g_last_error, sizeof(g_last_error), "device allocation of %zu bytes: %s",
+                      bytes, cudaGetErrorName(e));
         cudaGetLastError();
         return EMIN_ERR_NOMEM;
     }
@@ -140,7 +213,7 @@ void dfree(emin_ctx *c, T *&p) {
     if (!p) return;
     for (size_t i = 0; i < c->dev_allocs.size(); ++i)
         if (c->dev_allocs[i] == static_cast<void *>(p)) {
-            cudaFree(c->dev_allocs[i]);
+            release_dev(c, c->dev_allocs[i]);
             c->dev_allocs.erase(c->dev_allocs.begin() + (long)i);
             break;
         }
@@ -544,11 +617,10 @@ int create_impl(emin_ctx *c, const int *A_rowptr, const int *A_col, const double
         EMIN_TRY(alloc_work(c, c->w64, true));
     }
     EMIN_TRY(alloc_work(c, c->aux, false));
-    if (cudaMallocHost((void **)&c->hstate, sizeof(DevState)) != cudaSuccess ||
-        cudaMallocHost((void **)&c->hint, 4 * sizeof(int)) != cudaSuccess) {
-        cudaGetLastError();
-        return EMIN_ERR_NOMEM;
-    }
+    c->host_blk = host_block_get();
+    if (!c->host_blk) return EMIN_ERR_NOMEM;
+    c->hstate = static_cast<DevState *>(c->host_blk);
+    c->hint = reinterpret_cast<int *>(static_cast<char *>(c->host_blk) + kHintOffset);
 
     EMIN_TRY(copy_in(c, c->Ap, A_rowptr, sizeof(int) * (n + 1), on_dev));
     EMIN_TRY(copy_in(c, c->Aj, A_col, sizeof(int) * c->nnz_a, on_dev));
@@ -830,6 +902,13 @@ void emin_default_opts(emin_opts *opts) {
 
 const char *emin_last_error(void) { return g_last_error; }
 
+int emin_trim_memory(void) {
+    std::lock_guard<std::mutex> lk(g_pool_mutex);
+    for (cudaMemPool_t pool : g_pools)
+        if (pool && cudaMemPoolTrimTo(pool, 0) != cudaSuccess) return cuda_status(cudaGetLastError());
+    return EMIN_OK;
+}
+
 const char *emin_strerror(int status) {
     switch (status) {
         case EMIN_OK: return "ok";
@@ -856,10 +935,9 @@ void emin_destroy(emin_ctx *c) {
         if (c->w32.gexec) cudaGraphExecDestroy(c->w32.gexec);
         for (cudaGraphExec_t g : {c->w64.gwhile, c->adj.gwhile, c->aux.gwhile, c->w32.gwhile})
             if (g) cudaGraphExecDestroy(g);
-        for (void *p : c->dev_allocs) cudaFree(p);
+        for (void *p : c->dev_allocs) release_dev(c, p);
         for (cudaEvent_t e : c->events) cudaEventDestroy(e);
-        if (c->hstate) cudaFreeHost(c->hstate);
-        if (c->hint) cudaFreeHost(c->hint);
+        host_block_put(c->host_blk);
         cudaGetLastError();
     }
     delete c;
@@ -895,6 +973,7 @@ int emin_create(emin_ctx **out, int n, int nc, int k, const int *A_rowptr, const
     if (nsm <= 0) nsm = 1;
     occ_rows = 8;   // 2048 resident threads per SM at 256 threads per block
     occ_warps = 8;
+    c->pool = device_pool(c->device);
     c->L.stream = c->stream;
     c->L.nsm = nsm;
     c->L.grid_rows = nsm * occ_rows;

@@ -38,7 +38,8 @@ SYMBOLS = ("emin_default_opts", "emin_create", "emin_set_values", "emin_reset", 
            "emin_energy", "emin_get_p", "emin_kprod", "emin_outer", "emin_backward",
            "emin_backward_unrolled",
            "emin_stats", "emin_sizes", "emin_strerror", "emin_destroy", "emin_set_timing",
-           "emin_timing", "emin_masked_product_noalloc", "emin_last_error")
+           "emin_timing", "emin_masked_product_noalloc", "emin_last_error",
+           "emin_trim_memory")
 
 
 class emin_opts(ctypes.Structure):
@@ -79,6 +80,7 @@ def lib():
                                   _VP, _VP, ctypes.POINTER(emin_opts), _I]
         L.emin_set_values.argtypes = [_VP, _VP, _VP, _VP, _I]
         L.emin_reset.argtypes = [_VP]
+        L.emin_trim_memory.argtypes = []
         L.emin_iterate.argtypes = [_VP, _I, _D, ctypes.POINTER(_I), ctypes.POINTER(_D)]
         L.emin_energy.argtypes = [_VP, ctypes.POINTER(_D)]
         L.emin_get_p.argtypes = [_VP, _VP, _I]
@@ -340,6 +342,11 @@ def emin_masked_product_noalloc(n, nc, A_rowptr, A_col, A_val, P_rowptr, P_col, 
 def emin_destroy(h):
     if h:
         lib().emin_destroy(h)
+
+
+def emin_trim_memory():
+    """Give the device memory cached by destroyed contexts back to the driver."""
+    _check(lib().emin_trim_memory(), "emin_trim_memory")
 
 
 # ---------------------------------------------------------------------------

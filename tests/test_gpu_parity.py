@@ -128,6 +128,43 @@ def test_resume_equals_single_call():
     assert np.array_equal(a.get_p(), P10)
 
 
+def test_pooled_memory_reuse():
+    """Context memory comes from a pool that keeps what destroyed contexts
+    free: contexts made after others were destroyed (on another stream too),
+    and one that outlives a destroyed neighbour and a trim of the pool, give
+    the same P bit for bit."""
+    import torch
+    from paper_2208_02995_gb300.emin import emin_trim_memory
+    prob = I.diffusion3d_fv(16, 3)
+    ref = ctx(prob, "mixed")
+    ref.iterate(10)
+    P = ref.get_p()
+    ref.close()
+    for _ in range(3):
+        c = ctx(prob, "mixed")
+        c.iterate(10)
+        assert np.array_equal(c.get_p(), P)
+        c.close()
+    live = ctx(prob, "mixed")
+    other = ctx(I.diffusion3d_fv(12, 3), "mixed")
+    other.iterate(5)
+    other.close()
+    emin_trim_memory()
+    live.iterate(10)
+    assert np.array_equal(live.get_p(), P)
+    live.close()
+    s = torch.cuda.Stream()
+    a = ctx(prob, "mixed", stream=s)
+    a.iterate(10)
+    Pa = a.get_p()
+    a.close()
+    b = ctx(prob, "mixed")
+    b.iterate(10)
+    assert np.array_equal(Pa, P) and np.array_equal(b.get_p(), P)
+    b.close()
+    emin_trim_memory()
+
+
 @pytest.mark.parametrize("tau", [0.3, 0.05])
 def test_energy_stop_test(tau):
     prob = I.aniso3d(12, 1e-3, 2)
