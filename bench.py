@@ -295,6 +295,7 @@ def run_ours(args, dist):
             "kprod_avg_us": kprod_avg_s * 1e6,
             "kernel_share": {"kprod_ms": tm["ms"][0], "kprod_launches": int(tm["launches"][0])},
             "P": out.cpu().numpy(),
+            "E": ctx.energy(),
         }
         ctx.close()
     if args.precision != "both" or args.workload != WORKLOAD:
@@ -390,8 +391,36 @@ def run_ours(args, dist):
     if not args.no_sgs:
         line["sgs"] = sgs_summary(prob, stream, dist)
     if dist.world == 1 and not args.no_cpu_baseline and dist.rank == 0:
-        line["cpu_baseline"] = cpu_baseline(prob)
+        line["cpu_baseline"], oracle_P, oracle_E = cpu_baseline(prob)
+        line["vs_oracle"] = versus_oracle(prob, results, oracle_P, oracle_E)
     return line
+
+
+def constraint_error(prob, P):
+    """max |P B_c - B| over all entries (the constraint of Eq. (10))."""
+    import numpy as np
+    rows = np.repeat(np.arange(prob.n), np.diff(prob.P_rowptr))
+    Bc = np.asarray(prob.Bc).reshape(prob.nc, prob.k)
+    B = np.asarray(prob.B).reshape(prob.n, prob.k)
+    worst = 0.0
+    for c in range(prob.k):
+        PB = np.bincount(rows, weights=P * Bc[prob.P_col, c], minlength=prob.n)
+        worst = max(worst, float(np.abs(PB - B[:, c]).max(initial=0.0)))
+    return worst
+
+
+def versus_oracle(prob, results, oracle_P, oracle_E):
+    """The timed runs' P (after the last timed step: set-up + 20 iterations)
+    against the oracle's P of the same workload and iteration count."""
+    import numpy as np
+    out = {"iterations": ITERS, "oracle_energy": oracle_E}
+    for prec, r in results.items():
+        out[prec] = {
+            "P_rel_fro": float(np.linalg.norm(r["P"] - oracle_P) / np.linalg.norm(oracle_P)),
+            "E_rel": abs(r["E"] - oracle_E) / abs(oracle_E),
+            "constraint_max_abs": constraint_error(prob, r["P"]),
+        }
+    return out
 
 
 TAUS = (0.1, 1e-3, 1e-6)
@@ -510,15 +539,17 @@ def run_e2e(prob, args, dist):
 
 def cpu_baseline(prob):
     """The FP64 oracle as it stands (single thread) on the host: one whole
-    minimisation (set-up + 20 iterations) of the same workload."""
+    minimisation (set-up + 20 iterations) of the same workload.  Returns the
+    timing line and the oracle's P and energy (untimed) for the parity fields."""
     from oracle.oracle import Oracle
     t = time.perf_counter()
     o = Oracle(prob)
-    o.minimize(ITERS, 0.0)
+    res = o.minimize(ITERS, 0.0)
     el = time.perf_counter() - t
-    return {"value": ITERS / el, "unit": "iterations/s", "cores": 1, "kind": "oracle",
+    line = {"value": ITERS / el, "unit": "iterations/s", "cores": 1, "kind": "oracle",
             "sample": "one whole minimisation (set-up + 20 iterations) of the 128^3 workload",
             "seconds": el}
+    return line, res["P"], o.energy(res["P"])
 
 
 # ---------------------------------------------------------------------------

@@ -530,7 +530,11 @@ struct PkPlan<double> {
 };
 
 // L consecutive entries (positions pos, pos + 32, ...) of one lane's row:
-// all records first, then the gathers of Y for the first M slots
+// all records first, then every gather of Y, then the products.  The gathers
+// carry no branch: a slot with no match in row l loads Y[0] (valid whenever
+// a row of the warp has entries of P, the only case that gets here) and a
+// select keeps its accumulator, so the loads of all L entries issue back to
+// back instead of one divergent branch per slot.
 template <class T, int L, int M>
 __device__ __forceinline__ void pk_entries(const PkPlan<T> &pl, int pos, int p0,
                                            const T *__restrict__ Y, T *acc) {
@@ -538,15 +542,23 @@ __device__ __forceinline__ void pk_entries(const PkPlan<T> &pl, int pos, int p0,
     unsigned int w[L];
 #pragma unroll
     for (int j = 0; j < L; ++j) pl.get(pos + 32 * j, a[j], w[j]);
+    T v[L][M];
 #pragma unroll
     for (int j = 0; j < L; ++j) {
-        const T *yl = Y + (p0 + ((int)w[j] >> 12));
+        const int off = p0 + ((int)w[j] >> 12);
 #pragma unroll
         for (int s = 0; s < M; ++s) {
             const unsigned int q = (w[j] >> (3 * s)) & 7u;
-            if (q < 4u) acc[s] = fmat(a[j], yl[q], acc[s]);
+            v[j][s] = Y[q < 4u ? off + (int)q : 0];
         }
     }
+#pragma unroll
+    for (int j = 0; j < L; ++j)
+#pragma unroll
+        for (int s = 0; s < M; ++s) {
+            const unsigned int q = (w[j] >> (3 * s)) & 7u;
+            acc[s] = (q < 4u) ? fmat(a[j], v[j][s], acc[s]) : acc[s];
+        }
 }
 
 template <class T, int M>
