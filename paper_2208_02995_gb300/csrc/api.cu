@@ -36,6 +36,7 @@ struct emin_ctx {
     double *Ginv = nullptr, *dinv = nullptr, *dsq = nullptr, *dhalf = nullptr, *rn = nullptr;
     bool fast_k1 = false;  // k = 1, rows of P <= 4: fused set-up / final kernels and SELL plan
     float *Ginv32 = nullptr, *dinv32 = nullptr;
+    float *dsq32 = nullptr;  // D^{-1/2} as floats (mixed k = 1 fast path)
     // the iteration runs on A^ = D^{-1/2} A D^{-1/2} (float and/or double)
     float *Ah32 = nullptr, *qv32 = nullptr;
     double *Ah64 = nullptr, *qv64 = nullptr;
@@ -469,17 +470,17 @@ int run_setup(emin_ctx *c) {
         if (mixed) {
             launch_setup_k1<float>(L, c->n, c->dpos, c->Av, c->Pp, c->Pj, c->Bc, c->B, c->P0_in,
                                    c->opts.rank_policy, c->dint, c->dint + 2, c->dsq, c->dhalf,
-                                   c->Ginv, c->qv32, c->P0, c->t32a);
+                                   c->dsq32, c->Ginv, c->qv32, c->P0, c->t32a);
             launch_to_float(L, c->Bc, c->Bc32, (long long)c->nc * c->k);
             launch_sell_values<float>(L, c->n, c->Ap, c->Aj, c->Av, c->dsq, c->sell_ptr, c->sa32,
-                                      c->sw, c->spk32);
+                                      c->sw, c->spk32, c->dsq32);
             form_sgs_values<float>(c, c->sgs_fval32, c->sgs_bval32, c->sgs_bfval32,
                                    c->sgs_bbval32);
             EMIN_TRY(start_pcg<float>(c, iter_ops32(c), c->w32, c->t32a));
         } else {
             launch_setup_k1<double>(L, c->n, c->dpos, c->Av, c->Pp, c->Pj, c->Bc, c->B, c->P0_in,
                                     c->opts.rank_policy, c->dint, c->dint + 2, c->dsq, c->dhalf,
-                                    c->Ginv, c->qv64, c->P0, c->t64c);
+                                    nullptr, c->Ginv, c->qv64, c->P0, c->t64c);
             launch_sell_values<double>(L, c->n, c->Ap, c->Aj, c->Av, c->dsq, c->sell_ptr, c->sa64);
             form_sgs_values<double>(c, c->sgs_fval64, c->sgs_bval64, c->sgs_bfval64,
                                     c->sgs_bbval64);
@@ -689,6 +690,7 @@ int create_impl(emin_ctx *c, const int *A_rowptr, const int *A_col, const double
             dfree(c, c->sw);
         }
         if (c->opts.precision == EMIN_MIXED) {
+            EMIN_TRY(dalloc(c, &c->dsq32, n));
             if (c->sw) EMIN_TRY(dalloc(c, &c->spk32, acc));
             else EMIN_TRY(dalloc(c, &c->sa32, acc));
         } else {

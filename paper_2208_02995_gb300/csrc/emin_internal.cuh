@@ -194,12 +194,14 @@ void launch_to_float(const Launch &L, const double *src, float *dst, long long c
 void launch_to_double(const Launch &L, const float *src, double *dst, long long count);
 
 void launch_diag_scales(const Launch &L, int n, const double *dinv, double *dsq, double *dhalf);
-// whole k = 1 set-up per row (rows of P with at most 4 entries); see setup_kernels.cu
+// whole k = 1 set-up per row (rows of P with at most 4 entries); see
+// setup_kernels.cu.  dsq32 (float path, may be null) receives D^{-1/2} as the
+// float it is taken in
 template <class Tit>
 void launch_setup_k1(const Launch &L, int n, const int *dpos, const double *Av, const int *Pp,
                      const int *Pj, const double *Bc, const double *B, const double *P0_in,
-                     int policy, int *flags, int *ndef, double *dsq, double *dhalf, double *Ginv,
-                     Tit *qv, double *P0, Tit *x0);
+                     int policy, int *flags, int *ndef, double *dsq, double *dhalf, float *dsq32,
+                     double *Ginv, Tit *qv, double *P0, Tit *x0);
 // P = P0 + D^{-1/2} X (+ least-norm constraint correction), k = 1, rows <= 4
 template <class Tx>
 void launch_final_k1(const Launch &L, int n, const int *Pp, const int *Pj, const double *Bc,
@@ -214,11 +216,13 @@ void launch_sell_plan(const Launch &L, int n, const int *Ap, const int *Aj, cons
                       const int *Pj, const int *sell_ptr, int *soff, unsigned short *smap,
                       unsigned int *sw, int *wide, int *dpos);
 // A^ in plan order into sa, or (float, spk non-null) interleaved with the
-// packed words sw into spk
+// packed words sw into spk; dsq32 (float, may be null): D^{-1/2} as floats
+// (when dsq holds float-exact values), read instead of narrowing dsq
 template <class T>
 void launch_sell_values(const Launch &L, int n, const int *Ap, const int *Aj, const double *Av,
                         const double *dsq, const int *sell_ptr, T *sa,
-                        const unsigned int *sw = nullptr, uint2 *spk = nullptr);
+                        const unsigned int *sw = nullptr, uint2 *spk = nullptr,
+                        const float *dsq32 = nullptr);
 template <class T>
 void launch_scale_a(const Launch &L, int n, const int *Ap, const int *Aj, const double *Av,
                     const double *dsq, T *Ahat);

@@ -3,6 +3,7 @@
 #include <cuda_runtime.h>
 
 #include "device_util.cuh"
+#include "convert.cuh"
 #include "emin_internal.cuh"
 
 namespace emin {
@@ -296,7 +297,8 @@ __device__ __forceinline__ void setup_row_k1(int i, const int *__restrict__ dpos
                                              const double *__restrict__ B,
                                              const double *__restrict__ P0_in, int policy,
                                              int *flags, int *ndef, double *dsq, double *dhalf,
-                                             double *Ginv, Tit *qv, double *P0, Tit *x0) {
+                                             float *dsq32, double *Ginv, Tit *qv, double *P0,
+                                             Tit *x0) {
     const int p0 = Pp[i], m = Pp[i + 1] - p0;
     double b[M], p[M];
 #pragma unroll
@@ -317,11 +319,14 @@ __device__ __forceinline__ void setup_row_k1(int i, const int *__restrict__ dpos
     // later use sees the same value), the FP64 path in double
     double sq, dh;
     if constexpr (sizeof(Tit) == 4) {
-        const float df = (float)d;
+        // conversions on the integer pipe (convert.cuh): the FP64 pipe is
+        // this kernel's bound
+        const float df = f64_to_f32_rn(d);
         const float sf = (df > 0.f && isfinite(df)) ? rsqrtf(df) : 1.f;
         if (!(df > 0.f) || !isfinite(df)) atomicOr(flags, F_DIAG);
-        sq = (double)sf;
-        dh = (double)(df * sf);
+        sq = f32_to_f64(sf);
+        dh = f32_to_f64(df * sf);
+        if (dsq32) dsq32[i] = sf;
     } else {
         sq = rsqrt_newton(d);
         dh = d * sq;
@@ -338,9 +343,9 @@ __device__ __forceinline__ void setup_row_k1(int i, const int *__restrict__ dpos
         // restore) by two Newton-Raphson steps for the reciprocal,
         // x <- x + x (1 - G x), from the float seed 1/|b|^2, each step
         // squaring the relative error (about 1e-7 -> 1e-14 -> 1e-28)
-        const float rf = rsqrtf((float)G);
-        r = (double)rf;
-        gi = (double)(rf * rf);
+        const float rf = rsqrtf(f64_to_f32_rn(G));
+        r = f32_to_f64(rf);
+        gi = f32_to_f64(rf * rf);
         gi = fma(gi, fma(-G, gi, 1.0), gi);
         gi = fma(gi, fma(-G, gi, 1.0), gi);
     } else if (G > 0.0) {
@@ -362,8 +367,8 @@ __device__ __forceinline__ void setup_row_k1(int i, const int *__restrict__ dpos
             const double pc = fma(b[s], c, p[s]);
             P0[p0 + s] = pc;
             if constexpr (sizeof(Tit) == 4) {
-                x0[p0 + s] = (float)dh * (float)pc;
-                qv[p0 + s] = (float)b[s] * (float)r;
+                x0[p0 + s] = f64_to_f32_rn(dh) * f64_to_f32_rn(pc);
+                qv[p0 + s] = f64_to_f32_rn(b[s]) * f64_to_f32_rn(r);
             } else {
                 x0[p0 + s] = dh * pc;
                 qv[p0 + s] = b[s] * r;
@@ -376,8 +381,8 @@ __global__ void k_setup_k1(int n, const int *__restrict__ dpos, const double *__
                            const int *__restrict__ Pp, const int *__restrict__ Pj,
                            const double *__restrict__ Bc, const double *__restrict__ B,
                            const double *__restrict__ P0_in, int policy, int *flags, int *ndef,
-                           double *dsq, double *dhalf, double *Ginv, Tit *qv, double *P0,
-                           Tit *x0) {
+                           double *dsq, double *dhalf, float *dsq32, double *Ginv, Tit *qv,
+                           double *P0, Tit *x0) {
     // rows in warp-uniform passes, so that each warp runs the body for the
     // largest row of P among its 32 rows (no FP64 work on absent slots)
     const int lane = threadIdx.x & 31;
@@ -393,19 +398,19 @@ __global__ void k_setup_k1(int n, const int *__restrict__ dpos, const double *__
             case 0:
             case 1:
                 setup_row_k1<Tit, 1>(i, dpos, Av, Pp, Pj, Bc, B, P0_in, policy, flags, ndef, dsq,
-                                     dhalf, Ginv, qv, P0, x0);
+                                     dhalf, dsq32, Ginv, qv, P0, x0);
                 break;
             case 2:
                 setup_row_k1<Tit, 2>(i, dpos, Av, Pp, Pj, Bc, B, P0_in, policy, flags, ndef, dsq,
-                                     dhalf, Ginv, qv, P0, x0);
+                                     dhalf, dsq32, Ginv, qv, P0, x0);
                 break;
             case 3:
                 setup_row_k1<Tit, 3>(i, dpos, Av, Pp, Pj, Bc, B, P0_in, policy, flags, ndef, dsq,
-                                     dhalf, Ginv, qv, P0, x0);
+                                     dhalf, dsq32, Ginv, qv, P0, x0);
                 break;
             default:
                 setup_row_k1<Tit, 4>(i, dpos, Av, Pp, Pj, Bc, B, P0_in, policy, flags, ndef, dsq,
-                                     dhalf, Ginv, qv, P0, x0);
+                                     dhalf, dsq32, Ginv, qv, P0, x0);
         }
     }
 }
@@ -430,7 +435,7 @@ __device__ __forceinline__ void final_row_k1(int i, const int *__restrict__ Pp,
 #pragma unroll
     for (int s = 0; s < M; ++s) {
         const bool h = s < m;
-        p[s] = h ? fma(f, (double)X[p0 + s], P0[p0 + s]) : 0.0;
+        p[s] = h ? fma(f, as_f64(X[p0 + s]), P0[p0 + s]) : 0.0;
         b[s] = (h && correct) ? Bc[Pj[p0 + s]] : 0.0;
     }
     if (correct) {
@@ -544,8 +549,8 @@ template <class T>
 __global__ void __launch_bounds__(kBlock)
 k_sell_values(int n, const int *__restrict__ Ap, const int *__restrict__ Aj,
               const double *__restrict__ Av, const double *__restrict__ dsq,
-              const int *__restrict__ sell_ptr, T *sa, const unsigned int *__restrict__ sw,
-              uint2 *spk) {
+              const float *__restrict__ dsq32, const int *__restrict__ sell_ptr, T *sa,
+              const unsigned int *__restrict__ sw, uint2 *spk) {
     constexpr int CAP = 256;
     __shared__ double sv[kBlock / 32][CAP];
     __shared__ int sc[kBlock / 32][CAP];
@@ -559,7 +564,8 @@ k_sell_values(int n, const int *__restrict__ Ap, const int *__restrict__ Aj,
         const int i = i0 + lane;
         const bool valid = i < n;
         const int e0 = valid ? Ap[i] : eb, rl = valid ? Ap[i + 1] - e0 : 0;
-        const double di = valid ? dsq[i] : 0.0;
+        const double di = (valid && !dsq32) ? dsq[i] : 0.0;
+        const float di32 = (valid && dsq32) ? dsq32[i] : 0.f;
         const bool staged = cnt <= CAP;
         if (staged)
             for (int t = lane; t < cnt; t += 32) {
@@ -573,7 +579,8 @@ k_sell_values(int n, const int *__restrict__ Ap, const int *__restrict__ Aj,
                 const double a = staged ? sv[w][e0 - eb + j] : Av[e0 + j];
                 const int l = staged ? sc[w][e0 - eb + j] : Aj[e0 + j];
                 if constexpr (sizeof(T) == 4)
-                    v = (float)di * (float)a * (float)dsq[l];
+                    v = dsq32 ? di32 * f64_to_f32_rn(a) * dsq32[l]
+                              : f64_to_f32_rn(di) * f64_to_f32_rn(a) * f64_to_f32_rn(dsq[l]);
                 else
                     v = di * a * dsq[l];
             }
@@ -691,21 +698,22 @@ void launch_restore(const Launch &L, int n, int k, const int *Pp, const int *Pj,
 template <class Tit>
 void launch_setup_k1(const Launch &L, int n, const int *dpos, const double *Av, const int *Pp,
                      const int *Pj, const double *Bc, const double *B, const double *P0_in,
-                     int policy, int *flags, int *ndef, double *dsq, double *dhalf, double *Ginv,
-                     Tit *qv, double *P0, Tit *x0) {
+                     int policy, int *flags, int *ndef, double *dsq, double *dhalf, float *dsq32,
+                     double *Ginv, Tit *qv, double *P0, Tit *x0) {
     if (n <= 0) return;
     k_setup_k1<Tit><<<grid_for(n, L.grid_rows), kBlock, 0, L.stream>>>(
-        n, dpos, Av, Pp, Pj, Bc, B, P0_in, policy, flags, ndef, dsq, dhalf, Ginv, qv, P0, x0);
+        n, dpos, Av, Pp, Pj, Bc, B, P0_in, policy, flags, ndef, dsq, dhalf, dsq32, Ginv, qv, P0,
+        x0);
     note_launch();
 }
 template void launch_setup_k1<float>(const Launch &, int, const int *, const double *,
                                      const int *, const int *, const double *, const double *,
                                      const double *, int, int *, int *, double *, double *,
-                                     double *, float *, double *, float *);
+                                     float *, double *, float *, double *, float *);
 template void launch_setup_k1<double>(const Launch &, int, const int *, const double *,
                                       const int *, const int *, const double *, const double *,
                                       const double *, int, int *, int *, double *, double *,
-                                      double *, double *, double *, double *);
+                                      float *, double *, double *, double *, double *);
 
 template <class Tx>
 void launch_final_k1(const Launch &L, int n, const int *Pp, const int *Pj, const double *Bc,
@@ -743,18 +751,18 @@ void launch_sell_plan(const Launch &L, int n, const int *Ap, const int *Aj, cons
 template <class T>
 void launch_sell_values(const Launch &L, int n, const int *Ap, const int *Aj, const double *Av,
                         const double *dsq, const int *sell_ptr, T *sa, const unsigned int *sw,
-                        uint2 *spk) {
+                        uint2 *spk, const float *dsq32) {
     if (n <= 0) return;
     k_sell_values<T><<<grid_for((long long)((n + 31) / 32) * 32, L.grid_rows), kBlock, 0,
-                       L.stream>>>(n, Ap, Aj, Av, dsq, sell_ptr, sa, sw, spk);
+                       L.stream>>>(n, Ap, Aj, Av, dsq, dsq32, sell_ptr, sa, sw, spk);
     note_launch();
 }
 template void launch_sell_values<float>(const Launch &, int, const int *, const int *,
                                         const double *, const double *, const int *, float *,
-                                        const unsigned int *, uint2 *);
+                                        const unsigned int *, uint2 *, const float *);
 template void launch_sell_values<double>(const Launch &, int, const int *, const int *,
                                          const double *, const double *, const int *, double *,
-                                         const unsigned int *, uint2 *);
+                                         const unsigned int *, uint2 *, const float *);
 
 void launch_diag_scales(const Launch &L, int n, const double *dinv, double *dsq, double *dhalf) {
     if (n <= 0) return;

@@ -24,6 +24,7 @@
 #include <vector>
 
 #include "device_util.cuh"
+#include "convert.cuh"
 #include "emin_internal.cuh"
 
 namespace emin {
@@ -56,8 +57,8 @@ __global__ void k_sgs_values(long long nops, const int *__restrict__ own,
         }
         const int e = aent[o];
         const double di = dsq[own[o]], a = Av[e], dl = dsq[Aj[e]];
-        if constexpr (sizeof(T) == 4)
-            val[o] = (float)di * (float)a * (float)dl;
+        if constexpr (sizeof(T) == 4)  // narrowing on the integer pipe (convert.cuh)
+            val[o] = f64_to_f32_rn(di) * f64_to_f32_rn(a) * f64_to_f32_rn(dl);
         else
             val[o] = di * a * dl;
     }
