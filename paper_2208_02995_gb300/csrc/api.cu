@@ -89,6 +89,11 @@ struct emin_ctx {
     int applied_seen = 0;
     std::vector<void *> dev_allocs;
     cudaMemPool_t pool = nullptr;  // stream-ordered pool of dev_allocs (null: cudaMalloc)
+    // create from host arrays: the value arrays are copied on a second
+    // stream while the context's stream validates the pattern and builds
+    // the plan
+    cudaStream_t side = nullptr;
+    cudaEvent_t side_ev = nullptr;
     void *host_blk = nullptr;      // pinned block holding hstate and hint
     // instrumentation
     int timing = 0;  // 0 off, else time the masked product of every timing-th iteration
@@ -623,30 +628,50 @@ int create_impl(emin_ctx *c, const int *A_rowptr, const int *A_col, const double
     c->hstate = static_cast<DevState *>(c->host_blk);
     c->hint = reinterpret_cast<int *>(static_cast<char *>(c->host_blk) + kHintOffset);
 
+    // the patterns first, on the context's stream
     EMIN_TRY(copy_in(c, c->Ap, A_rowptr, sizeof(int) * (n + 1), on_dev));
     EMIN_TRY(copy_in(c, c->Aj, A_col, sizeof(int) * c->nnz_a, on_dev));
-    EMIN_TRY(copy_in(c, c->Av, A_val, sizeof(double) * c->nnz_a, on_dev));
     EMIN_TRY(copy_in(c, c->Pp, P_rowptr, sizeof(int) * (n + 1), on_dev));
     EMIN_TRY(copy_in(c, c->Pj, P_col, sizeof(int) * c->nnz_p, on_dev));
-    EMIN_TRY(copy_in(c, c->P0_in, P0_val, sizeof(double) * c->nnz_p, on_dev));
-    EMIN_TRY(copy_in(c, c->B, B, sizeof(double) * nk, on_dev));
-    EMIN_TRY(copy_in(c, c->Bc, Bc, sizeof(double) * nck, on_dev));
+    // the values: from host arrays on the second stream (ordered after the
+    // allocations, which are stream-ordered on the context's stream), so
+    // that the host link keeps copying while the pattern is validated and
+    // the plan is built; the value checks and the set-up wait for them
+    const bool split = !on_dev && (c->nnz_a > 0 || c->nnz_p > 0);
+    cudaStream_t cs = c->stream;
+    if (split) {
+        if (!c->side) {
+            EMIN_TRY(cuda_status(cudaStreamCreateWithFlags(&c->side, cudaStreamNonBlocking)));
+            EMIN_TRY(cuda_status(cudaEventCreateWithFlags(&c->side_ev, cudaEventDisableTiming)));
+        }
+        EMIN_TRY(cuda_status(cudaEventRecord(c->side_ev, c->stream)));
+        EMIN_TRY(cuda_status(cudaStreamWaitEvent(c->side, c->side_ev, 0)));
+        cs = c->side;
+    }
+    auto copy_values = [&](void *dst, const void *src, size_t bytes) -> int {
+        if (bytes == 0) return EMIN_OK;
+        if (!src) return EMIN_ERR_ARG;
+        return cuda_status(cudaMemcpyAsync(
+            dst, src, bytes, on_dev ? cudaMemcpyDeviceToDevice : cudaMemcpyHostToDevice, cs));
+    };
+    EMIN_TRY(copy_values(c->Av, A_val, sizeof(double) * c->nnz_a));
+    EMIN_TRY(copy_values(c->P0_in, P0_val, sizeof(double) * c->nnz_p));
+    EMIN_TRY(copy_values(c->B, B, sizeof(double) * nk));
+    EMIN_TRY(copy_values(c->Bc, Bc, sizeof(double) * nck));
+    if (split) EMIN_TRY(cuda_status(cudaEventRecord(c->side_ev, c->side)));
 
-    // validate on the device before any kernel indexes through the arrays
+    // validate the patterns on the device before any kernel indexes through
+    // them (the values are checked once they have arrived, below; their
+    // flag is read with the set-up's)
     EMIN_TRY(cuda_status(cudaMemsetAsync(c->dint, 0, 4 * sizeof(int), c->stream)));
     launch_validate_csr(c->L, n, n, c->Ap, (int)c->nnz_a, c->Aj, c->dint, c->dint + 3);
     launch_validate_csr(c->L, n, c->nc, c->Pp, (int)c->nnz_p, c->Pj, c->dint, c->dint + 1);
-    launch_check_finite(c->L, c->Av, c->nnz_a, c->dint);
-    launch_check_finite(c->L, c->P0_in, c->nnz_p, c->dint);
-    launch_check_finite(c->L, c->B, nk, c->dint);
-    launch_check_finite(c->L, c->Bc, nck, c->dint);
     EMIN_TRY(check_launch());
     EMIN_TRY(cuda_status(cudaMemcpyAsync(c->hint, c->dint, 4 * sizeof(int), cudaMemcpyDeviceToHost,
                                          c->stream)));
     EMIN_TRY(sync(c));
     const int f = c->hint[0];
     if (f & (F_ROWPTR | F_COL | F_ORDER)) return EMIN_ERR_PATTERN;
-    if (f & F_NONFINITE) return EMIN_ERR_ARG;
     c->maxrow_p = c->hint[1];
     if (c->maxrow_p > kMaxRowP) return EMIN_ERR_ARG;
     c->lanes = (c->maxrow_p <= 8) ? 1 : 32;
@@ -746,7 +771,17 @@ int create_impl(emin_ctx *c, const int *A_rowptr, const int *A_col, const double
 
     if (c->opts.precond == EMIN_SGS && n > 0) EMIN_TRY(build_sgs(c));
 
+    if (split) EMIN_TRY(cuda_status(cudaStreamWaitEvent(c->stream, c->side_ev, 0)));
     EMIN_TRY(run_setup(c));
+    // the value checks after the set-up (which clears the flags first): a
+    // non-finite value only makes the set-up's arithmetic non-finite, no
+    // index depends on it, and read_flags reports it before any flag the
+    // set-up raised
+    launch_check_finite(c->L, c->Av, c->nnz_a, c->dint);
+    launch_check_finite(c->L, c->P0_in, c->nnz_p, c->dint);
+    launch_check_finite(c->L, c->B, nk, c->dint);
+    launch_check_finite(c->L, c->Bc, nck, c->dint);
+    EMIN_TRY(check_launch());
     return read_flags(c);
 }
 
@@ -931,6 +966,7 @@ void emin_destroy(emin_ctx *c) {
     if (!c) return;
     {
         DeviceGuard g(c->device);
+        if (c->side) cudaStreamSynchronize(c->side);
         cudaStreamSynchronize(c->stream);
         for (cudaGraphExec_t g : {c->w64.gexec, c->adj.gexec, c->aux.gexec})
             if (g) cudaGraphExecDestroy(g);
@@ -940,6 +976,8 @@ void emin_destroy(emin_ctx *c) {
         for (void *p : c->dev_allocs) release_dev(c, p);
         for (cudaEvent_t e : c->events) cudaEventDestroy(e);
         host_block_put(c->host_blk);
+        if (c->side_ev) cudaEventDestroy(c->side_ev);
+        if (c->side) cudaStreamDestroy(c->side);
         cudaGetLastError();
     }
     delete c;

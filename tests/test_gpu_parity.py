@@ -265,6 +265,34 @@ def test_invalid_inputs_are_rejected():
     _expect(E.EMIN_ERR_DIAG, mod(A_val=v))
     v = base.A_val.copy(); v[3] = np.nan
     _expect(E.EMIN_ERR_ARG, mod(A_val=v))
+    # non-finite values of the other inputs (checked once the value copies,
+    # which overlap the plan build, have arrived)
+    b = base.B.copy(); b.reshape(-1)[0] = np.inf
+    _expect(E.EMIN_ERR_ARG, mod(B=b))
+    bc = base.Bc.copy(); bc.reshape(-1)[1] = np.nan
+    _expect(E.EMIN_ERR_ARG, mod(Bc=bc))
+    p0 = base.P0_val.copy(); p0[2] = -np.inf
+    _expect(E.EMIN_ERR_ARG, mod(P0_val=p0))
+
+
+@pytest.mark.parametrize("precision", ["fp64", "mixed"])
+def test_host_and_device_inputs_agree(precision):
+    """Host inputs are copied in two streams (values beside the plan build),
+    device inputs on one: the same P bit for bit."""
+    import torch
+    from paper_2208_02995_gb300.emin import Context
+    for prob in (I.diffusion3d_fv(16, 3), I.elasticity3d(5, 0.3, 3)):
+        a = ctx(prob, precision)
+        a.iterate(8)
+        Pa = a.get_p()
+        dev = [torch.from_numpy(np.ascontiguousarray(x)).cuda() for x in prob.arrays()]
+        torch.cuda.synchronize()
+        b = Context(n=prob.n, nc=prob.nc, k=prob.k, arrays=dev, precision=precision)
+        b.iterate(8)
+        out = torch.empty(prob.nnz_p, dtype=torch.float64, device="cuda")
+        b.get_p(out)
+        torch.cuda.synchronize()
+        assert np.array_equal(Pa, out.cpu().numpy())
 
 
 def test_rank_policy():
