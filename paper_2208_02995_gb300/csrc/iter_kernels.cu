@@ -578,8 +578,13 @@ __device__ __forceinline__ void pk_row(const PkPlan<T> &pl, int pos, int len, in
     }
 }
 
+// 512 threads: the 16 warps of a block take 16 consecutive slices per pass, so
+// more of a slice's neighbours in the second grid direction (4 slices away in
+// the 3D workloads) are gathered by a sibling warp of the same SM; 768 threads
+// (2 blocks per SM) measured slower
+constexpr int kPkBlock = 512;
 template <class T>
-__global__ void __launch_bounds__(kBlock)
+__global__ void __launch_bounds__(kPkBlock)
 k_kprod_k1_pk(int n, const int *__restrict__ sell_ptr, PkPlan<T> pl, const int *__restrict__ Pp,
               const T *__restrict__ qv, const T *__restrict__ Y, T *__restrict__ out, int project,
               int dot_mode, DevState *st, double *partials, double *hist, int cap,
@@ -837,8 +842,10 @@ void launch_kprod(const Launch &L, const Ops<T> &o, const T *Y, T *out, int proj
             pl.w = o.sw;
         }
         const long long warps = (o.n + 31) / 32;
-        const int g = grid_for(warps * 32, sizeof(T) == 4 ? L.grid_pk32 : L.grid_pk64);
-        k_kprod_k1_pk<T><<<g, kBlock, 0, L.stream>>>(o.n, o.sell_ptr, pl, o.Pp, o.qv, Y, out,
+        const long long need = (warps * 32 + kPkBlock - 1) / kPkBlock;
+        const int cap = sizeof(T) == 4 ? L.grid_pk32 : L.grid_pk64;
+        const int g = (int)(need < cap ? (need > 0 ? need : 1) : cap);
+        k_kprod_k1_pk<T><<<g, kPkBlock, 0, L.stream>>>(o.n, o.sell_ptr, pl, o.Pp, o.qv, Y, out,
                                                       project, dot_mode, w.st, w.partials, w.hist,
                                                       w.hist_cap, check_stop);
     } else if (o.k == 1 && o.sell_ptr && o.sa && o.qv && o.maxrow <= 4) {
@@ -933,8 +940,8 @@ int pk_blocks_per_sm(int double_precision) {
     int nb = 0;
     const cudaError_t e =
         double_precision
-            ? cudaOccupancyMaxActiveBlocksPerMultiprocessor(&nb, k_kprod_k1_pk<double>, kBlock, 0)
-            : cudaOccupancyMaxActiveBlocksPerMultiprocessor(&nb, k_kprod_k1_pk<float>, kBlock, 0);
+            ? cudaOccupancyMaxActiveBlocksPerMultiprocessor(&nb, k_kprod_k1_pk<double>, kPkBlock, 0)
+            : cudaOccupancyMaxActiveBlocksPerMultiprocessor(&nb, k_kprod_k1_pk<float>, kPkBlock, 0);
     if (e != cudaSuccess) {
         cudaGetLastError();
         nb = 1;
