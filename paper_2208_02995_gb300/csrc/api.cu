@@ -1025,6 +1025,10 @@ int emin_create(emin_ctx **out, int n, int nc, int k, const int *A_rowptr, const
     if (c->L.grid_pk32 > kMaxGrid) c->L.grid_pk32 = kMaxGrid;
     c->L.grid_pk64 = nsm * pk_blocks_per_sm(1);
     if (c->L.grid_pk64 > kMaxGrid) c->L.grid_pk64 = kMaxGrid;
+    c->L.grid_flat32 = nsm * flat_blocks_per_sm(0);
+    if (c->L.grid_flat32 > kMaxGrid) c->L.grid_flat32 = kMaxGrid;
+    c->L.grid_flat64 = nsm * flat_blocks_per_sm(1);
+    if (c->L.grid_flat64 > kMaxGrid) c->L.grid_flat64 = kMaxGrid;
     if (c->L.grid_warps > kMaxGrid) c->L.grid_warps = kMaxGrid;
     set_iter_attributes();
     set_adjoint_attributes();

@@ -161,6 +161,8 @@ struct Launch {
     int nsm;          // streaming multiprocessors of the device
     int grid_pk32;    // resident grids of the packed-plan masked product (float, double)
     int grid_pk64;
+    int grid_flat32;  // resident grids of the flat vector streams (float, double)
+    int grid_flat64;
 };
 
 // shared-memory slots per warp for a row of P: the longest row rounded up
@@ -247,6 +249,7 @@ void launch_state_reset(const Launch &L, DevState *st);
 void set_iter_attributes();
 int staged_blocks_per_sm();
 int pk_blocks_per_sm(int double_precision);
+int flat_blocks_per_sm(int double_precision);
 
 // projected block SGS (sgs.cu)
 struct SgsHost {

@@ -687,51 +687,57 @@ __device__ __forceinline__ double2 axpy4(double b, double2 y, double2 r) {
 }
 
 // y~ = z~ + beta y~ (z~ = r~ for Jacobi; R is z~)
+// the flat streams ask for 8 resident blocks (2048 threads) per SM and are
+// launched as one resident wave (Launch::grid_flat*)
 template <class T>
-__global__ void __launch_bounds__(kBlock)
+__global__ void __launch_bounds__(kBlock, 8)
 k_ydir_flat(long long count, const T *__restrict__ R, T *__restrict__ Y, const DevState *st) {
     if (st->stop) return;
     const T beta = (T)st->beta;
     using V = typename Vec<T>::V;
     constexpr int W = Vec<T>::W;
-    const long long nv = count / W;
-    const long long stride = (long long)gridDim.x * blockDim.x;
+    // 32-bit unsigned indices: value arrays on P's pattern have fewer than
+    // 2^31 entries (int32 row pointers), so no index or step passes 2^32
+    const unsigned nv = (unsigned)(count / W), cnt = (unsigned)count;
+    const unsigned stride = gridDim.x * blockDim.x;
     const V *R4 = reinterpret_cast<const V *>(R);
     V *Y4 = reinterpret_cast<V *>(Y);
-    for (long long v = blockIdx.x * (long long)blockDim.x + threadIdx.x; v < nv; v += stride)
+    for (unsigned v = blockIdx.x * blockDim.x + threadIdx.x; v < nv; v += stride)
         Y4[v] = axpy4(beta, Y4[v], R4[v]);
-    for (long long q = nv * W + blockIdx.x * (long long)blockDim.x + threadIdx.x; q < count;
-         q += stride)
+    for (unsigned q = nv * W + blockIdx.x * blockDim.x + threadIdx.x; q < cnt; q += stride)
         Y[q] = fmat(beta, Y[q], R[q]);
 }
 
 // dW~ += alpha y~, r~ -= alpha y_~ (UPD_STEP, UPD_XR), then gamma = <r~, r~>
 // (UPD_STEP, UPD_INIT) or <r~, z~> (UPD_GZ_*, Z given); UPD_FLOOR sets the
 // convergence floor from <r~, r~>.
-template <class T>
-__device__ __forceinline__ void upd1(T &r, T &x, T y, T yb, T alpha, int mode, Dot<T> &dot) {
+template <class T, int MODE>
+__device__ __forceinline__ void upd1(T &r, T &x, T y, T yb, T alpha, Dot<T> &dot) {
     x = fmat(alpha, y, x);
     r = fmat(-alpha, yb, r);
-    if (mode == UPD_STEP) dot.add(r, r);
+    if constexpr (MODE == UPD_STEP) dot.add(r, r);
 }
 
-template <class T>
-__global__ void __launch_bounds__(kBlock)
+// one instantiation per mode, so that each carries only its own path
+template <class T, int MODE>
+__global__ void __launch_bounds__(kBlock, 8)
 k_update_flat(long long count, T *__restrict__ R, const T *__restrict__ Y,
               const T *__restrict__ Yb, T *__restrict__ X, DevState *st, double *partials,
-              int mode, const T *__restrict__ Z) {
+              const T *__restrict__ Z) {
+    constexpr int mode = MODE;
     if (mode != UPD_FLOOR && st->stop) return;
     const T alpha = (T)st->alpha;
     using V = typename Vec<T>::V;
     constexpr int W = Vec<T>::W;
-    const long long nv = count / W;
-    const long long stride = (long long)gridDim.x * blockDim.x;
+    // 32-bit unsigned indices (see k_ydir_flat)
+    const unsigned nv = (unsigned)(count / W), cnt = (unsigned)count;
+    const unsigned stride = gridDim.x * blockDim.x;
     Dot<T> dot;
-    const bool step = (mode == UPD_STEP || mode == UPD_XR);
-    const bool gz = (mode == UPD_GZ_INIT || mode == UPD_GZ_STEP);
-    for (long long v = blockIdx.x * (long long)blockDim.x + threadIdx.x; v < nv; v += stride) {
+    constexpr bool step = (mode == UPD_STEP || mode == UPD_XR);
+    constexpr bool gz = (mode == UPD_GZ_INIT || mode == UPD_GZ_STEP);
+    for (unsigned v = blockIdx.x * blockDim.x + threadIdx.x; v < nv; v += stride) {
         V r = reinterpret_cast<V *>(R)[v];
-        if (gz) {
+        if constexpr (gz) {
             const V z = reinterpret_cast<const V *>(Z)[v];
             dot.add(r.x, z.x);
             dot.add(r.y, z.y);
@@ -739,15 +745,15 @@ k_update_flat(long long count, T *__restrict__ R, const T *__restrict__ Y,
                 dot.add(r.z, z.z);
                 dot.add(r.w, z.w);
             }
-        } else if (step) {
+        } else if constexpr (step) {
             V x = reinterpret_cast<V *>(X)[v];
             const V y = reinterpret_cast<const V *>(Y)[v];
             const V yb = reinterpret_cast<const V *>(Yb)[v];
-            upd1(r.x, x.x, y.x, yb.x, alpha, mode, dot);
-            upd1(r.y, x.y, y.y, yb.y, alpha, mode, dot);
+            upd1<T, MODE>(r.x, x.x, y.x, yb.x, alpha, dot);
+            upd1<T, MODE>(r.y, x.y, y.y, yb.y, alpha, dot);
             if constexpr (W == 4) {
-                upd1(r.z, x.z, y.z, yb.z, alpha, mode, dot);
-                upd1(r.w, x.w, y.w, yb.w, alpha, mode, dot);
+                upd1<T, MODE>(r.z, x.z, y.z, yb.z, alpha, dot);
+                upd1<T, MODE>(r.w, x.w, y.w, yb.w, alpha, dot);
             }
             reinterpret_cast<V *>(X)[v] = x;
             reinterpret_cast<V *>(R)[v] = r;
@@ -760,21 +766,20 @@ k_update_flat(long long count, T *__restrict__ R, const T *__restrict__ Y,
             }
         }
     }
-    for (long long q = nv * W + blockIdx.x * (long long)blockDim.x + threadIdx.x; q < count;
-         q += stride) {
+    for (unsigned q = nv * W + blockIdx.x * blockDim.x + threadIdx.x; q < cnt; q += stride) {
         T r = R[q];
-        if (gz) {
+        if constexpr (gz) {
             dot.add(r, Z[q]);
-        } else if (step) {
+        } else if constexpr (step) {
             T x = X[q];
-            upd1(r, x, Y[q], Yb[q], alpha, mode, dot);
+            upd1<T, MODE>(r, x, Y[q], Yb[q], alpha, dot);
             X[q] = x;
             R[q] = r;
         } else {
             dot.add(r, r);
         }
     }
-    if (mode == UPD_XR) return;  // no reduction: gamma follows the preconditioner
+    if constexpr (mode == UPD_XR) return;  // no reduction: gamma follows the preconditioner
     __shared__ double sh[32];
     double bt = block_dot_total(dot, sh);
     double total;
@@ -899,7 +904,8 @@ void launch_project(const Launch &L, const Ops<T> &o, T *x, T scale) {
 template <class T>
 void launch_ydir(const Launch &L, long long count, Work<T> &w) {
     if (count <= 0) return;
-    const int g = grid_for((count + Vec<T>::W - 1) / Vec<T>::W, L.grid_rows);
+    const int g = grid_for((count + Vec<T>::W - 1) / Vec<T>::W,
+                           sizeof(T) == 4 ? L.grid_flat32 : L.grid_flat64);
     k_ydir_flat<T><<<g, kBlock, 0, L.stream>>>(count, w.Z ? w.Z : w.R, w.Y, w.st);
     note_launch();
 }
@@ -907,10 +913,47 @@ void launch_ydir(const Launch &L, long long count, Work<T> &w) {
 template <class T>
 void launch_update(const Launch &L, long long count, Work<T> &w, int mode) {
     if (count <= 0) return;
-    const int g = grid_for((count + Vec<T>::W - 1) / Vec<T>::W, L.grid_rows);
-    k_update_flat<T><<<g, kBlock, 0, L.stream>>>(count, w.R, w.Y, w.Yb, w.X, w.st, w.partials,
-                                                  mode, w.Z);
+    const int g = grid_for((count + Vec<T>::W - 1) / Vec<T>::W,
+                           sizeof(T) == 4 ? L.grid_flat32 : L.grid_flat64);
+    switch (mode) {
+#define EMIN_UPD(M)                                                                           \
+    case M:                                                                                   \
+        k_update_flat<T, M><<<g, kBlock, 0, L.stream>>>(count, w.R, w.Y, w.Yb, w.X, w.st,    \
+                                                        w.partials, w.Z);                     \
+        break;
+        EMIN_UPD(UPD_INIT)
+        EMIN_UPD(UPD_STEP)
+        EMIN_UPD(UPD_FLOOR)
+        EMIN_UPD(UPD_XR)
+        EMIN_UPD(UPD_GZ_INIT)
+        EMIN_UPD(UPD_GZ_STEP)
+#undef EMIN_UPD
+        default: return;
+    }
     note_launch();
+}
+
+// Resident grid of the flat streams (direction and update kernels): the
+// blocks per SM of the hot update (and of the direction kernel, whichever is
+// smaller), so that a launch is one full wave.
+int flat_blocks_per_sm(int double_precision) {
+    int a = 0, b = 0;
+    cudaError_t e1, e2;
+    if (double_precision) {
+        e1 = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&a, k_update_flat<double, UPD_STEP>,
+                                                           kBlock, 0);
+        e2 = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&b, k_ydir_flat<double>, kBlock, 0);
+    } else {
+        e1 = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&a, k_update_flat<float, UPD_STEP>,
+                                                           kBlock, 0);
+        e2 = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&b, k_ydir_flat<float>, kBlock, 0);
+    }
+    if (e1 != cudaSuccess || e2 != cudaSuccess) {
+        cudaGetLastError();
+        return 1;
+    }
+    const int nb = a < b ? a : b;
+    return nb > 0 ? nb : 1;
 }
 
 template <class Tin, class Tout>
