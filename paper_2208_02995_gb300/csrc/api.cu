@@ -344,14 +344,21 @@ int start_pcg(emin_ctx *c, const Ops<T> &o, Work<T> &w, const T *x0) {
         EMIN_TRY(cuda_status(cudaMemsetAsync(w.Y, 0, sizeof(T) * c->nnz_p, c->stream)));
         EMIN_TRY(cuda_status(cudaMemsetAsync(w.X, 0, sizeof(T) * c->nnz_p, c->stream)));
     }
-    if (x0) launch_kprod<T>(c->L, o, x0, w.R, 0, DOT_NONE, w, 0);
-    launch_update<T>(c->L, c->nnz_p, w, UPD_FLOOR);
-    launch_project<T>(c->L, o, w.R, x0 ? T(-1) : T(1));
-    if (o.sgs.ngroups > 0) {
+    // on the packed k = 1 plan one launch forms r~, the floor and (Jacobi)
+    // gamma_0; otherwise the product, the floor, the projection and gamma_0
+    // are separate passes
+    const bool sgs = o.sgs.ngroups > 0;
+    const bool fused = x0 && launch_kprod_start<T>(c->L, o, x0, w.R, w, sgs ? 0 : 1);
+    if (!fused) {
+        if (x0) launch_kprod<T>(c->L, o, x0, w.R, 0, DOT_NONE, w, 0);
+        launch_update<T>(c->L, c->nnz_p, w, UPD_FLOOR);
+        launch_project<T>(c->L, o, w.R, x0 ? T(-1) : T(1));
+    }
+    if (sgs) {
         // z~_0 = Pi (L^ + I)^{-T} (L^ + I)^{-1} r~_0, gamma_0 = <r~, z~>
         launch_sgs_sweep<T>(c->L, o.sgs, w.R, w.Z, w.st);
         launch_sgs_finish<T>(c->L, o, w, 1, c->nnz_p);
-    } else {
+    } else if (!fused) {
         launch_update<T>(c->L, c->nnz_p, w, UPD_INIT);
     }
     return check_launch();

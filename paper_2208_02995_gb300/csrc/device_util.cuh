@@ -84,6 +84,39 @@ __device__ __forceinline__ bool grid_reduce(double block_total, double *partials
     return threadIdx.x == 0;
 }
 
+// Two sums reduced at once, deterministically (as grid_reduce): partials
+// holds 2 gridDim.x doubles; returns true in thread 0 of the last block,
+// with *ta and *tb set.
+__device__ __forceinline__ bool grid_reduce2(double a, double b, double *partials,
+                                             unsigned int *ticket, double *ta, double *tb) {
+    __shared__ bool am_last;
+    __shared__ double sh[32];
+    if (threadIdx.x == 0) {
+        partials[blockIdx.x] = a;
+        partials[gridDim.x + blockIdx.x] = b;
+        __threadfence();
+        unsigned int t = atomicAdd(ticket, 1u);
+        am_last = (t == gridDim.x - 1);
+    }
+    __syncthreads();
+    if (!am_last) return false;
+    __threadfence();
+    double sa = 0.0, sb = 0.0;
+    for (int k = threadIdx.x; k < (int)gridDim.x; k += blockDim.x) {
+        sa += __ldcg(partials + k);
+        sb += __ldcg(partials + gridDim.x + k);
+    }
+    sa = block_sum(sa, sh);
+    __syncthreads();
+    sb = block_sum(sb, sh);
+    if (threadIdx.x == 0) {
+        *ta = sa;
+        *tb = sb;
+        *ticket = 0u;
+    }
+    return threadIdx.x == 0;
+}
+
 // Warp totals of a Dot accumulator gathered into one double per block.
 template <class T>
 __device__ __forceinline__ double block_dot_total(Dot<T> &d, double *sh) {

@@ -60,7 +60,9 @@ struct DevState {
 };
 
 // reduction targets of the masked-product kernel
-enum DotMode : int { DOT_NONE = 0, DOT_ALPHA = 1, DOT_AUX = 2 };
+// (DOT_START: the start of Algorithm 3 on the packed k = 1 plan, see
+// launch_kprod_start)
+enum DotMode : int { DOT_NONE = 0, DOT_ALPHA = 1, DOT_AUX = 2, DOT_START = 3 };
 // modes of the update kernel: UPD_STEP applies the step and forms gamma =
 // <r~, r~> (Jacobi: z = r); UPD_INIT forms gamma_0; UPD_FLOOR sets the
 // convergence floor from the residual; with another preconditioner the step
@@ -237,6 +239,13 @@ void launch_kprod(const Launch &L, const Ops<T> &o, const T *Y, T *out, int proj
                   int dot_mode, Work<T> &w, int check_stop);
 template <class T>
 void launch_project(const Launch &L, const Ops<T> &o, T *x, T scale);
+// The start of Algorithm 3 in one launch when the packed k = 1 plan serves
+// the product: R = -Pi mask(A^ x0), the convergence floor from the
+// unprojected product and (gamma0 != 0, Jacobi) gamma_0 = <R, R>.  Returns
+// false (nothing launched) for any other plan.
+template <class T>
+bool launch_kprod_start(const Launch &L, const Ops<T> &o, const T *x0, T *R, Work<T> &w,
+                        int gamma0);
 template <class T>
 void launch_ydir(const Launch &L, long long count, Work<T> &w);
 template <class T>

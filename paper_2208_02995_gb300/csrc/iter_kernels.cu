@@ -583,12 +583,19 @@ __device__ __forceinline__ void pk_row(const PkPlan<T> &pl, int pos, int len, in
 // the 3D workloads) are gathered by a sibling warp of the same SM; 768 threads
 // (2 blocks per SM) measured slower
 constexpr int kPkBlock = 512;
-template <class T>
+// DM, the reduction (one instantiation each, so that the product of the
+// iteration, DOT_ALPHA, carries nothing else): DOT_NONE, DOT_ALPHA
+// (y^T y_ -> alpha), DOT_AUX (y^T y_ -> aux), or DOT_START: out = -Pi(A^ x0)
+// with the floor's <r, r> taken before the projection and (gamma0) gamma_0
+// = <r~, r~> after it, reduced together.
+template <class T, int DM>
 __global__ void __launch_bounds__(kPkBlock)
 k_kprod_k1_pk(int n, const int *__restrict__ sell_ptr, PkPlan<T> pl, const int *__restrict__ Pp,
               const T *__restrict__ qv, const T *__restrict__ Y, T *__restrict__ out, int project,
-              int dot_mode, DevState *st, double *partials, double *hist, int cap,
+              int gamma0, DevState *st, double *partials, double *hist, int cap,
               int check_stop) {
+    constexpr bool dot_mode = (DM == DOT_ALPHA || DM == DOT_AUX);
+    Dot<T> dot0, dot1;  // DOT_START: the sums before and after the projection
     if (check_stop && st->stop) return;
     const int lane = threadIdx.x & 31;
     const int nslices = (n + 31) >> 5;
@@ -622,6 +629,11 @@ k_kprod_k1_pk(int n, const int *__restrict__ sell_ptr, PkPlan<T> pl, const int *
             case 3: pk_row<T, 3>(pl, pos, len, p0, Y, x); break;
             default: pk_row<T, 4>(pl, pos, len, p0, Y, x); break;
         }
+        if constexpr (DM == DOT_START) {
+#pragma unroll
+            for (int s = 0; s < 4; ++s)
+                if (s < m) dot0.add(x[s], x[s]);
+        }
         if (project) {
             T t = T(0);
 #pragma unroll
@@ -632,17 +644,32 @@ k_kprod_k1_pk(int n, const int *__restrict__ sell_ptr, PkPlan<T> pl, const int *
 #pragma unroll
         for (int s = 0; s < 4; ++s)
             if (s < m) {
-                out[p0 + s] = x[s];
-                if (dot_mode) dot.add(yown[s], x[s]);
+                if constexpr (DM == DOT_START) {
+                    out[p0 + s] = -x[s];
+                    if (gamma0) dot1.add(x[s], x[s]);
+                } else {
+                    out[p0 + s] = x[s];
+                }
+                if constexpr (dot_mode) dot.add(yown[s], x[s]);
             }
     }
-    if (dot_mode) {
+    if constexpr (dot_mode) {
         __shared__ double sh[32];
         double bt = block_dot_total(dot, sh);
         double total;
         if (grid_reduce(bt, partials, &st->ticket[0], &total)) {
-            if (dot_mode == DOT_ALPHA) finalize_alpha(st, total, hist, cap);
+            if (DM == DOT_ALPHA) finalize_alpha(st, total, hist, cap);
             else st->aux = total;
+        }
+    } else if constexpr (DM == DOT_START) {
+        __shared__ double sh[32];
+        const double b0 = block_dot_total(dot0, sh);
+        __syncthreads();
+        const double b1 = block_dot_total(dot1, sh);
+        double s0, s1;
+        if (grid_reduce2(b0, b1, partials, &st->ticket[0], &s0, &s1)) {
+            finalize_gamma(st, s0, UPD_FLOOR, GammaFloor<T>::value);
+            if (gamma0) finalize_gamma(st, s1, UPD_INIT, GammaFloor<T>::value);
         }
     }
 }
@@ -829,6 +856,22 @@ inline int grid_for(long long work, int cap) {
 
 }  // namespace
 
+// Resident blocks per SM of one instantiation of the packed product (the
+// instantiations hold different register counts), queried once.
+template <class T, int DM>
+int pk_per_sm() {
+    static const int per_sm = [] {
+        int nb = 0;
+        if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&nb, k_kprod_k1_pk<T, DM>, kPkBlock,
+                                                          0) != cudaSuccess) {
+            cudaGetLastError();
+            nb = 1;
+        }
+        return nb > 0 ? nb : 1;
+    }();
+    return per_sm;
+}
+
 template <class T>
 void launch_kprod(const Launch &L, const Ops<T> &o, const T *Y, T *out, int project, int dot_mode,
                   Work<T> &w, int check_stop) {
@@ -848,11 +891,25 @@ void launch_kprod(const Launch &L, const Ops<T> &o, const T *Y, T *out, int proj
         }
         const long long warps = (o.n + 31) / 32;
         const long long need = (warps * 32 + kPkBlock - 1) / kPkBlock;
-        const int cap = sizeof(T) == 4 ? L.grid_pk32 : L.grid_pk64;
-        const int g = (int)(need < cap ? (need > 0 ? need : 1) : cap);
-        k_kprod_k1_pk<T><<<g, kPkBlock, 0, L.stream>>>(o.n, o.sell_ptr, pl, o.Pp, o.qv, Y, out,
-                                                      project, dot_mode, w.st, w.partials, w.hist,
-                                                      w.hist_cap, check_stop);
+        // one resident wave of the instantiation that runs (the iteration's
+        // DOT_ALPHA product: L.grid_pk*, from the same query at create)
+        switch (dot_mode) {
+#define EMIN_PK(DMV)                                                                       \
+    case DMV: {                                                                            \
+        long long cap = (long long)L.nsm * pk_per_sm<T, DMV>();                            \
+        if (cap > kMaxGrid) cap = kMaxGrid;                                                \
+        const int g = (int)(need < cap ? (need > 0 ? need : 1) : cap);                    \
+        k_kprod_k1_pk<T, DMV><<<g, kPkBlock, 0, L.stream>>>(o.n, o.sell_ptr, pl, o.Pp, o.qv, \
+                                                            Y, out, project, 0, w.st,        \
+                                                            w.partials, w.hist, w.hist_cap,  \
+                                                            check_stop);                     \
+    } break;
+            EMIN_PK(DOT_NONE)
+            EMIN_PK(DOT_ALPHA)
+            EMIN_PK(DOT_AUX)
+#undef EMIN_PK
+            default: return;
+        }
     } else if (o.k == 1 && o.sell_ptr && o.sa && o.qv && o.maxrow <= 4) {
         if constexpr (sizeof(T) == 4) {
             // one block per group of 8 slices, at most the resident grid
@@ -899,6 +956,34 @@ void launch_project(const Launch &L, const Ops<T> &o, T *x, T scale) {
         k_project_warp<T><<<grid_for((long long)o.n * 32, L.grid_rows), kBlock, 0, L.stream>>>(
             o.n, o.k, o.Pp, o.Pj, o.Bc, o.Ginv, x, scale);
     note_launch();
+}
+
+template <class T>
+bool launch_kprod_start(const Launch &L, const Ops<T> &o, const T *x0, T *R, Work<T> &w,
+                        int gamma0) {
+    if (o.n <= 0 || (o.boff && o.blen && o.bmap)) return false;
+    if (!(o.k == 1 && o.sell_ptr && o.sw && o.qv && o.maxrow <= 4 &&
+          (sizeof(T) == 4 ? o.spk != nullptr : o.sa != nullptr)))
+        return false;
+    PkPlan<T> pl;
+    if constexpr (sizeof(T) == 4) {
+        pl.e = o.spk;
+    } else {
+        pl.a = o.sa;
+        pl.w = o.sw;
+    }
+    const long long warps = (o.n + 31) / 32;
+    const long long need = (warps * 32 + kPkBlock - 1) / kPkBlock;
+    // one resident wave of this instantiation (it holds more registers than
+    // the iteration's product)
+    const long long cap = (long long)L.nsm * pk_per_sm<T, DOT_START>();
+    int g = (int)(need < cap ? (need > 0 ? need : 1) : cap);
+    if (2 * g > kMaxGrid) g = kMaxGrid / 2;  // two partial sums per block
+    k_kprod_k1_pk<T, DOT_START><<<g, kPkBlock, 0, L.stream>>>(
+        o.n, o.sell_ptr, pl, o.Pp, o.qv, x0, R, 1, gamma0, w.st, w.partials, w.hist, w.hist_cap,
+        0);
+    note_launch();
+    return true;
 }
 
 template <class T>
@@ -980,16 +1065,18 @@ int staged_blocks_per_sm() {
 }
 
 int pk_blocks_per_sm(int double_precision) {
-    int nb = 0;
-    const cudaError_t e =
-        double_precision
-            ? cudaOccupancyMaxActiveBlocksPerMultiprocessor(&nb, k_kprod_k1_pk<double>, kPkBlock, 0)
-            : cudaOccupancyMaxActiveBlocksPerMultiprocessor(&nb, k_kprod_k1_pk<float>, kPkBlock, 0);
-    if (e != cudaSuccess) {
-        cudaGetLastError();
-        nb = 1;
+    // every instantiation's query is made here, at create, and not first
+    // inside a graph capture; the iteration's product is DOT_ALPHA
+    if (double_precision) {
+        pk_per_sm<double, DOT_NONE>();
+        pk_per_sm<double, DOT_AUX>();
+        pk_per_sm<double, DOT_START>();
+        return pk_per_sm<double, DOT_ALPHA>();
     }
-    return nb > 0 ? nb : 1;
+    pk_per_sm<float, DOT_NONE>();
+    pk_per_sm<float, DOT_AUX>();
+    pk_per_sm<float, DOT_START>();
+    return pk_per_sm<float, DOT_ALPHA>();
 }
 
 void set_iter_attributes() {
@@ -1019,6 +1106,10 @@ template void launch_kprod<float>(const Launch &, const Ops<float> &, const floa
                                   int, Work<float> &, int);
 template void launch_project<double>(const Launch &, const Ops<double> &, double *, double);
 template void launch_project<float>(const Launch &, const Ops<float> &, float *, float);
+template bool launch_kprod_start<double>(const Launch &, const Ops<double> &, const double *,
+                                         double *, Work<double> &, int);
+template bool launch_kprod_start<float>(const Launch &, const Ops<float> &, const float *,
+                                        float *, Work<float> &, int);
 template void launch_ydir<double>(const Launch &, long long, Work<double> &);
 template void launch_ydir<float>(const Launch &, long long, Work<float> &);
 template void launch_update<double>(const Launch &, long long, Work<double> &, int);
