@@ -640,10 +640,12 @@ int create_impl(emin_ctx *c, const int *A_rowptr, const int *A_col, const double
     EMIN_TRY(copy_in(c, c->Aj, A_col, sizeof(int) * c->nnz_a, on_dev));
     EMIN_TRY(copy_in(c, c->Pp, P_rowptr, sizeof(int) * (n + 1), on_dev));
     EMIN_TRY(copy_in(c, c->Pj, P_col, sizeof(int) * c->nnz_p, on_dev));
-    // the values: from host arrays on the second stream (ordered after the
-    // allocations, which are stream-ordered on the context's stream), so
-    // that the host link keeps copying while the pattern is validated and
-    // the plan is built; the value checks and the set-up wait for them
+    // the values: from host arrays on the second stream, ordered after the
+    // pattern copies (and the allocations, which are stream-ordered on the
+    // context's stream) so that the patterns, which the plan build needs
+    // first, have the host link to themselves; the values then cross it
+    // while the pattern is validated and the plan is built, and the value
+    // checks and the set-up wait for them
     const bool split = !on_dev && (c->nnz_a > 0 || c->nnz_p > 0);
     cudaStream_t cs = c->stream;
     if (split) {
