@@ -100,6 +100,9 @@ class Dist:
 # ---------------------------------------------------------------------------
 # algorithmic work of one masked-product launch (Section 4; k = 1 here)
 # ---------------------------------------------------------------------------
+NOMINAL_HBM_GBS = 8000.0  # GB300 HBM3e, nominal (the measured copy rate is the roofline)
+
+
 def kprod_bytes(prob, vbytes: int) -> int:
     """A (values + column indices + row pointers), P's pattern, Y read once,
     Y_ written once, the per-row inverse Gram factor and B_c."""
@@ -314,6 +317,7 @@ def run_ours(args, dist):
     K = args.steps
     value = dist.world * ITERS * K / (m["ms"] / 1e3)
     b32 = kprod_bytes(prob, 4)
+    traffic = captured_traffic()
     ach = b32 / (m["kprod_avg_us"] * 1e-6) / 1e9
     f = results["fp64"]
     fl = kprod_flops(prob, hits)
@@ -351,10 +355,15 @@ def run_ours(args, dist):
             "peak": hbm_peak,
             "unit": "GB/s",
             "frac": ach / hbm_peak,
-            "traffic": captured_traffic(),
+            "traffic": traffic,
             "algorithmic_bytes": b32,
             "avg_launch_us": m["kprod_avg_us"],
             "peak_source": hbm_src,
+            # the same launch against the nominal HBM3e rate, the DRAM rate the
+            # ncu traffic implies at the loop's launch time, and the products
+            "frac_of_nominal_8tbs": ach / NOMINAL_HBM_GBS,
+            "dram_gbs": (traffic / (m["kprod_avg_us"] * 1e-6) / 1e9) if traffic else None,
+            "in_pattern_products_per_s": hits / (m["kprod_avg_us"] * 1e-6),
         },
         "fp64": {
             "value": dist.world * ITERS * K / (f["ms"] / 1e3),
