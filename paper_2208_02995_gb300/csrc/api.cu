@@ -1030,10 +1030,8 @@ int emin_create(emin_ctx **out, int n, int nc, int k, const int *A_rowptr, const
     if (c->L.grid_rows > kMaxGrid) c->L.grid_rows = kMaxGrid;
     c->L.grid_staged = nsm * staged_blocks_per_sm();
     if (c->L.grid_staged > kMaxGrid) c->L.grid_staged = kMaxGrid;
-    c->L.grid_pk32 = nsm * pk_blocks_per_sm(0);
-    if (c->L.grid_pk32 > kMaxGrid) c->L.grid_pk32 = kMaxGrid;
-    c->L.grid_pk64 = nsm * pk_blocks_per_sm(1);
-    if (c->L.grid_pk64 > kMaxGrid) c->L.grid_pk64 = kMaxGrid;
+    pk_blocks_per_sm(0);  // occupancy of every packed-product instantiation, queried now
+    pk_blocks_per_sm(1);
     c->L.grid_flat32 = nsm * flat_blocks_per_sm(0);
     if (c->L.grid_flat32 > kMaxGrid) c->L.grid_flat32 = kMaxGrid;
     c->L.grid_flat64 = nsm * flat_blocks_per_sm(1);

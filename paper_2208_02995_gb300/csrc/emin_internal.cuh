@@ -161,8 +161,6 @@ struct Launch {
     int grid_warps;   // grid of warp-per-row kernels
     int grid_staged;  // resident grid of the staged masked product
     int nsm;          // streaming multiprocessors of the device
-    int grid_pk32;    // resident grids of the packed-plan masked product (float, double)
-    int grid_pk64;
     int grid_flat32;  // resident grids of the flat vector streams (float, double)
     int grid_flat64;
 };
@@ -257,6 +255,8 @@ void launch_row_scale(const Launch &L, int n, const int *Pp, int lanes, const do
 void launch_state_reset(const Launch &L, DevState *st);
 void set_iter_attributes();
 int staged_blocks_per_sm();
+// resident blocks per SM of the packed product's iteration launch; also makes
+// every instantiation's occupancy query at create, outside any graph capture
 int pk_blocks_per_sm(int double_precision);
 int flat_blocks_per_sm(int double_precision);
 

@@ -891,8 +891,7 @@ void launch_kprod(const Launch &L, const Ops<T> &o, const T *Y, T *out, int proj
         }
         const long long warps = (o.n + 31) / 32;
         const long long need = (warps * 32 + kPkBlock - 1) / kPkBlock;
-        // one resident wave of the instantiation that runs (the iteration's
-        // DOT_ALPHA product: L.grid_pk*, from the same query at create)
+        // one resident wave of the instantiation that runs (queried at create)
         switch (dot_mode) {
 #define EMIN_PK(DMV)                                                                       \
     case DMV: {                                                                            \
