@@ -43,7 +43,7 @@ METRIC = ("restricted-PCG iterations/s and masked A·P effective HBM GB/s "
           "(% of peak), FP32 vs FP64")
 WORKLOAD = 2
 ITERS = 20
-FP64_PEAK_TFLOPS = 1.25  # nominal GB300 FP64 (no measured FP64 peak on this machine)
+FP64_PEAK_TFLOPS = 1.25  # nominal GB300 FP64 (152 SMs x 2 FMA/clk x 2 flops x 2.07 GHz)
 
 
 def parse():
@@ -55,6 +55,8 @@ def parse():
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-e2e", action="store_true")
     ap.add_argument("--no-tau", action="store_true", help="skip the time-to-tau measurement")
+    ap.add_argument("--no-workloads", action="store_true",
+                    help="skip the record of the other workloads (1, 3, 4, 5)")
     ap.add_argument("--no-sgs", action="store_true", help="skip the SGS preconditioner summary")
     ap.add_argument("--precond", choices=["jacobi", "sgs"], default="jacobi",
                     help="preconditioner of the timed runs (the headline is Jacobi)")
@@ -137,6 +139,48 @@ def in_pattern_products(prob) -> tuple[int, int]:
     return cand, hits
 
 
+def in_pattern_products_blocked(prob, nb=3, kb=6):
+    """(candidate, in-pattern) products of one mask_P(A Y) for a node-blocked
+    problem (nb dofs per node, columns of P in groups of kb per aggregate,
+    the nb rows of a node sharing their patterns): every stored nb x nb block
+    (v, b) of A contributes nb*nb*|J_b| candidates and nb*nb*|J_v & J_b|
+    in-pattern products, counted at node level from the aggregate sets."""
+    import numpy as np
+    nn = prob.n // nb
+    Ap, Aj, Pp, Pj = prob.A_rowptr, prob.A_col, prob.P_rowptr, prob.P_col
+    na = np.diff(Pp[0:prob.n + 1:nb]) // (nb * kb)  # aggregates per node
+    w = int(na.max())
+    S = np.full((nn, w), -1, dtype=np.int64)
+    first = Pp[0:prob.n:nb]
+    for q in range(w):
+        has = na > q
+        S[has, q] = Pj[first[has] + kb * q] // kb
+    # node neighbours: the nb rows of a node hold nb * deg entries each
+    deg = np.diff(Ap[0:prob.n + 1:nb]) // (nb * nb)
+    v = np.repeat(np.arange(nn), deg)
+    row0 = Ap[0:prob.n:nb]
+    j = np.arange(len(v)) - np.repeat(np.cumsum(deg) - deg, deg)
+    b = Aj[row0[v] + nb * j] // nb
+    cand = int(nb * nb * kb * na[b].sum())
+    hits = 0
+    for s0 in range(0, len(v), 1 << 20):
+        Sv, Sb = S[v[s0:s0 + (1 << 20)]], S[b[s0:s0 + (1 << 20)]]
+        eq = (Sv[:, :, None] == Sb[:, None, :]) & (Sv[:, :, None] >= 0)
+        hits += int(eq.sum())
+    return cand, nb * nb * kb * hits
+
+
+def products(prob):
+    """(candidate, in-pattern) products of one masked product, or (0, 0)
+    when neither counting scheme applies."""
+    import numpy as np
+    if int(np.diff(prob.P_rowptr).max(initial=0)) <= 8:
+        return in_pattern_products(prob)
+    if prob.k == 6 and prob.n % 3 == 0 and prob.meta.get("kind") == "elasticity":
+        return in_pattern_products_blocked(prob)
+    return 0, 0
+
+
 def captured_traffic():
     """DRAM bytes per launch of the dominant kernel from the committed ncu
     summary, or None when the kernel sources changed since that capture."""
@@ -180,17 +224,26 @@ class Clocks:
         self.proc = None
         self.path = None
 
-    def start(self):
+    def start(self, period_ms: int = 10):
+        """Start sampling every period_ms and wait (at most 5 s) until the
+        first sample is written, so that the timed region that follows is
+        covered from its start."""
         import tempfile
         try:
             fd, self.path = tempfile.mkstemp(suffix=".csv")
             os.close(fd)
             self.proc = subprocess.Popen(
                 ["nvidia-smi", f"--id={self.index}", f"--query-gpu={self.Q}",
-                 "--format=csv,noheader,nounits", "-lms", "50"],
+                 "--format=csv,noheader,nounits", "-lms", str(period_ms)],
                 stdout=open(self.path, "w"), stderr=subprocess.DEVNULL)
         except (OSError, FileNotFoundError):
             self.proc = None
+            return
+        t_end = time.time() + 5.0
+        while time.time() < t_end and self.proc.poll() is None:
+            if os.path.getsize(self.path) > 0:
+                break
+            time.sleep(0.01)
 
     def stop(self):
         if not self.proc:
@@ -251,6 +304,21 @@ def time_steps(ctx, out, K, W, stream, dist, iters=ITERS):
     return t0.elapsed_time(t1)
 
 
+def headline_config(dist):
+    """The workload of the headline line, shared by both arms."""
+    return {
+        "workload": ("3D 7-point FV diffusion 128^3 (n=2,097,152, nnz(A)=14,581,760), "
+                     "log-normal kappa sigma=2 seed 2, k=1, 3x3x3 aggregates "
+                     "(n_c=74,088), nnz(P)=6,127,616, 20 restricted PCG iterations"),
+        "step": "set-up + 20 iterations + final P, inputs resident in HBM",
+        "precision": "FP32 vs FP64: value = mixed (float A/P/products, double Gram "
+                     "factorisation, reductions and final constraint restore), key fp64 = "
+                     "plain FP64; the reference arm is the FP64 oracle",
+        "l2": "inputs larger than L2 (A 175 MB + P vectors 123 MB > 129 MB)",
+        "parallelism": f"replicas x{dist.world}",
+    }
+
+
 def run_ours(args, dist):
     import numpy as np
     import torch
@@ -270,7 +338,7 @@ def run_ours(args, dist):
     hbm_peak = float(peaks.get("hbm_gbs", 6800.0))
     hbm_src = "measured" if "hbm_gbs" in peaks else "fallback"
 
-    cand, hits = in_pattern_products(prob) if int(np.diff(prob.P_rowptr).max()) <= 8 else (0, 0)
+    cand, hits = products(prob)
     stream = torch.cuda.Stream()
     results = {}
     precs = ("mixed", "fp64") if args.precision == "both" else (args.precision,)
@@ -322,6 +390,7 @@ def run_ours(args, dist):
     f = results["fp64"]
     fl = kprod_flops(prob, hits)
     ach64 = fl / (f["kprod_avg_us"] * 1e-6) / 1e12
+    f64peak = fp64_peak(stream)
     b64 = kprod_bytes(prob, 8)
     line = {
         "metric": METRIC,
@@ -336,18 +405,7 @@ def run_ours(args, dist):
         "vs_baseline": None,
         "dtype": "f32",
         "data": "synthetic",
-        "config": {
-            "workload": ("3D 7-point FV diffusion 128^3 (n=2,097,152, nnz(A)=14,581,760), "
-                         "log-normal kappa sigma=2 seed 2, k=1, 3x3x3 aggregates "
-                         "(n_c=74,088), nnz(P)=6,127,616, 20 restricted PCG iterations"),
-            "step": "set-up + 20 iterations + final P, inputs resident in HBM",
-            "precision": "mixed: float A/P/products, double Gram factorisation, "
-                         "reductions and final constraint restore",
-            "l2": "inputs larger than L2 (A 175 MB + P vectors 123 MB > 129 MB)",
-            "parallelism": f"replicas x{dist.world}",
-            "candidate_products": cand,
-            "in_pattern_products": hits,
-        },
+        "config": headline_config(dist),
         "roofline": {
             "kernel": "masked product + projection + y^T y_ (k_kprod_k1_pk<float>, packed SELL-32 plan)",
             "bound": "hbm",
@@ -364,6 +422,8 @@ def run_ours(args, dist):
             "frac_of_nominal_8tbs": ach / NOMINAL_HBM_GBS,
             "dram_gbs": (traffic / (m["kprod_avg_us"] * 1e-6) / 1e9) if traffic else None,
             "in_pattern_products_per_s": hits / (m["kprod_avg_us"] * 1e-6),
+            "candidate_products": cand,
+            "in_pattern_products": hits,
         },
         "fp64": {
             "value": dist.world * ITERS * K / (f["ms"] / 1e3),
@@ -374,14 +434,17 @@ def run_ours(args, dist):
                 "kernel": "masked product + projection + y^T y_ (k_kprod_k1_pk<double>, packed SELL-32 plan)",
                 "bound": "alu",
                 "achieved": ach64,
-                "peak": FP64_PEAK_TFLOPS,
+                "peak": f64peak["tflops"],
                 "unit": "TFLOP/s",
-                "frac": ach64 / FP64_PEAK_TFLOPS,
+                "frac": ach64 / f64peak["tflops"],
                 "traffic": None,
                 "flops": fl,
                 "hbm_gbs": b64 / (f["kprod_avg_us"] * 1e-6) / 1e9,
                 "avg_launch_us": f["kprod_avg_us"],
-                "peak_source": "nominal FP64 rate of GB300 (152 SMs x 2 FP64 FMA/clk x 2070 MHz)",
+                "peak_source": f64peak["source"],
+                "peak_nominal": FP64_PEAK_TFLOPS,
+                "frac_of_nominal": ach64 / FP64_PEAK_TFLOPS,
+                "peak_nominal_source": "152 SMs x 2 FP64 FMA/clk x 2 flops x 2070 MHz",
             },
             "gpu_launches": f["gpu_launches"],
         },
@@ -395,6 +458,20 @@ def run_ours(args, dist):
             "time_to_P_ratio": f["ms"] / m["ms"],
         },
     }
+    if not args.no_workloads:
+        clk = Clocks(dist.local)
+        clk.start()
+        wl = {"2": {"workload": line["config"]["workload"], "note": "the headline above",
+                    "mixed": {"iterations_per_s": value, "kprod_avg_us": m["kprod_avg_us"],
+                              "kprod_frac_hbm": ach / hbm_peak},
+                    "fp64": {"iterations_per_s": line["fp64"]["value"],
+                             "kprod_avg_us": f["kprod_avg_us"],
+                             "kprod_frac_fp64": ach64 / f64peak["tflops"]}}}
+        for w in sorted(WORKLOAD_STEPS):
+            wl[str(w)] = run_workload(w, args, dist, stream, hbm_peak, f64peak)
+        wl["clocks"] = clk.stop()
+        wl["peaks"] = {"hbm_gbs": hbm_peak, "hbm_source": hbm_src, "fp64": f64peak}
+        line["workloads"] = wl
     if not args.no_tau:
         line["time_to_tau"] = time_to_tau(prob, stream)
     if not args.no_sgs:
@@ -403,6 +480,100 @@ def run_ours(args, dist):
         line["cpu_baseline"], oracle_P, oracle_E = cpu_baseline(prob)
         line["vs_oracle"] = versus_oracle(prob, results, oracle_P, oracle_E)
     return line
+
+
+# the other workloads of the metric (the headline is workload 2): (warm-up,
+# timed steps) per workload, sized so that each arm takes a few seconds; the
+# oracle's P after the same iterations is compared where it finishes in
+# seconds on the host
+WORKLOAD_STEPS = {1: (5, 20), 3: (3, 10), 4: (3, 10), 5: (3, 4)}
+ORACLE_PARITY = (1, 4)
+BACKWARD = (4, 5)  # workloads whose configuration includes the implicit adjoint
+
+
+def fp64_peak(stream):
+    """Measured FP64 FMA rate of this GPU (TFLOP/s) from the library's probe,
+    best of three launches, with the nominal rate for reference."""
+    from paper_2208_02995_gb300.emin import emin_fma_rate
+    best = max(emin_fma_rate("fp64", stream)[0] for _ in range(3))
+    return {"tflops": 2.0 * best / 1e12, "source": "measured: emin_fma_rate (independent "
+            "DFMA chains on every SM, CUDA events, best of 3)", "nominal_tflops": FP64_PEAK_TFLOPS}
+
+
+def run_workload(w, args, dist, stream, hbm_peak, f64peak):
+    """One record of the per-workload table: both precisions, the masked
+    product's average CUDA-event time per launch against its roofline, the
+    adjoint where the configuration names it, the oracle's P where it is fast."""
+    import numpy as np
+    import torch
+
+    from paper_2208_02995_gb300 import inputs
+    from paper_2208_02995_gb300.emin import Context, emin_set_timing, emin_timing
+    prob = inputs.config(w)
+    cand, hits = products(prob)
+    W, K = WORKLOAD_STEPS[w]
+    rec = {"workload": inputs.CONFIG_NAMES[w], "n": prob.n, "nnz_a": prob.nnz_a,
+           "nnz_p": prob.nnz_p, "nc": prob.nc, "k": prob.k, "iterations": prob.iters,
+           "candidate_products": cand, "in_pattern_products": hits, "warmup": W, "steps": K,
+           "step": f"set-up + {prob.iters} iterations + final P, inputs resident in HBM"}
+    Ps = {}
+    for prec in ("mixed", "fp64"):
+        with torch.cuda.stream(stream):
+            ctx = Context(prob, precision=prec, stream=stream)
+            out = torch.empty(prob.nnz_p, dtype=torch.float64, device="cuda")
+        emin_set_timing(ctx.h, 1)
+        ms = time_steps(ctx, out, K, W, stream, dist, prob.iters)
+        tm = emin_timing(ctx.h)
+        emin_set_timing(ctx.h, 0)
+        ms = dist.max(ms)
+        kus = tm["ms"][0] / max(tm["launches"][0], 1) * 1e3
+        v = 4 if prec == "mixed" else 8
+        b = kprod_bytes(prob, v)
+        r = {"ms_per_step": ms / K, "iterations_per_s": dist.world * prob.iters * K / (ms / 1e3),
+             "kprod_avg_us": kus, "kprod_launches": int(tm["launches"][0]),
+             "kprod_algorithmic_bytes": b, "kprod_gbs": b / (kus * 1e-6) / 1e9}
+        r["kprod_frac_hbm"] = r["kprod_gbs"] / hbm_peak
+        if prec == "fp64" and hits:
+            fl = kprod_flops(prob, hits)
+            r["kprod_flops"] = fl
+            r["kprod_tflops"] = fl / (kus * 1e-6) / 1e12
+            r["kprod_frac_fp64"] = r["kprod_tflops"] / f64peak["tflops"]
+        if w in BACKWARD:
+            # L = tr(P^T A P) + ||P||_F^2 of the P just formed; the adjoint runs
+            # as many restricted PCG steps as the forward
+            _, dE, _ = ctx.energy_grad(out, 1.0, want_energy=False, want_dX=True)
+            dLdP = dE + 2.0 * out
+            ctx.backward(dLdP, prob.iters, 0.0)
+            torch.cuda.synchronize()
+            t = time.perf_counter()
+            reps = 3
+            for _ in range(reps):
+                ctx.backward(dLdP, prob.iters, 0.0)
+            torch.cuda.synchronize()
+            r["backward_ms"] = (time.perf_counter() - t) / reps * 1e3
+            r["backward"] = (f"implicit adjoint (FP64), {prob.iters} restricted PCG steps, "
+                             "mask_P(A U), mask_A(U P^T), G^-1 B^T; host-timed per call")
+        Ps[prec] = (out.cpu().numpy(), ctx.energy())
+        rec[prec] = r
+        ctx.close()
+        del ctx, out
+        torch.cuda.empty_cache()
+    rec["mixed_vs_fp64_P_rel"] = float(np.linalg.norm(Ps["mixed"][0] - Ps["fp64"][0]) /
+                                       np.linalg.norm(Ps["fp64"][0]))
+    rec["time_to_P_ratio"] = rec["fp64"]["ms_per_step"] / rec["mixed"]["ms_per_step"]
+    if w in ORACLE_PARITY and dist.rank == 0:
+        from oracle.oracle import Oracle
+        o = Oracle(prob)
+        ref = o.minimize(prob.iters, 0.0)
+        Eref = o.energy(ref["P"])
+        rec["vs_oracle"] = {p: {"P_rel_fro": float(np.linalg.norm(Ps[p][0] - ref["P"]) /
+                                                    np.linalg.norm(ref["P"])),
+                                "E_rel": abs(Ps[p][1] - Eref) / abs(Eref),
+                                "constraint_max_abs": constraint_error(prob, Ps[p][0])}
+                            for p in Ps}
+    else:
+        rec["constraint_max_abs"] = {p: constraint_error(prob, Ps[p][0]) for p in Ps}
+    return rec
 
 
 def constraint_error(prob, P):
@@ -569,17 +740,23 @@ def run_reference(args, dist):
     from paper_2208_02995_gb300 import inputs
 
     prob = inputs.config(WORKLOAD)
-    # each step is one whole minimisation when K + W steps fit in ~4 minutes,
-    # else a bounded sample of fewer iterations (same set-up)
-    budget_s, est_step_s = 240.0, 12.0
-    its = ITERS if (args.steps + args.warmup) * est_step_s <= budget_s else \
-        max(1, int(ITERS * budget_s / ((args.steps + args.warmup) * est_step_s)))
+    its = ITERS
 
     def step():
         o = Oracle(prob)
         o.minimize(its, 0.0)
 
-    for _ in range(args.warmup):
+    # the first warm-up step (one whole minimisation) is timed on the host:
+    # every step stays a whole minimisation when the remaining steps fit in
+    # about 4 minutes, else each is a bounded sample of fewer iterations
+    budget_s = 240.0
+    t = time.perf_counter()
+    step()
+    first_s = time.perf_counter() - t
+    rest = args.steps + max(args.warmup - 1, 0)
+    if rest * first_s > budget_s:
+        its = max(1, int(ITERS * budget_s / (rest * first_s)))
+    for _ in range(args.warmup - 1):
         step()
     t = time.perf_counter()
     for _ in range(args.steps):
@@ -593,8 +770,8 @@ def run_reference(args, dist):
         "n_gpus": dist.world, "steps": args.steps, "warmup": args.warmup,
         "ms_per_step": el / args.steps * 1e3, "higher_is_better": True, "scaling": "weak",
         "vs_baseline": None, "dtype": "f64", "data": "synthetic",
-        "config": {"workload": "3D 7-point FV diffusion 128^3, k=1, 3x3x3 aggregates, "
-                               "20 restricted PCG iterations", "precision": "fp64 (oracle)"},
+        "config": headline_config(dist),
+        "arm": "the FP64 CPU oracle (plain C, single thread) on the host cores",
         "cpu_baseline": {"value": value, "unit": "iterations/s", "cores": 1, "kind": "oracle",
                          "sample": sample},
         "e2e": {"value": value, "unit": "iterations/s", "h2d_bytes_per_step": 0,

@@ -165,6 +165,19 @@ int emin_kprod(emin_ctx *ctx, const double *X, double *out, int project, int on_
 int emin_outer(emin_ctx *ctx, const double *U, const double *V, double *out, int on_device);
 
 /*
+ * Energy of a given X on P's pattern and its gradient (Eq. (trace),
+ * E = tr(X^T A X) = <X, mask_P(A X)>), in double on the stored (unscaled) A:
+ *   *E        = <X, mask_P(A X)>              (host double; may be NULL)
+ *   dE_dX     = scale * 2 mask_P(A X)         (nnz(P); may be NULL; A symmetric)
+ *   dE_dAval  = scale * mask_A(X X^T)         (nnz(A), per stored entry; may be NULL)
+ * scale multiplies both gradients (an upstream derivative of the caller's
+ * loss, 1 for the plain gradient).  X and the gradient arrays are device or
+ * host per `on_device`.  Independent of the iteration state.
+ */
+int emin_energy_grad(emin_ctx *ctx, const double *X, double scale, double *E,
+                     double *dE_dX, double *dE_dAval, int on_device);
+
+/*
  * Implicit adjoint of the converged minimiser P* (not in the paper; derived
  * from the saddle-point system (sadsys)).  Given dL/dP on P's pattern it
  * solves Pi K Pi u = 1/2 Pi dL/dP by the same restricted PCG (in double,
@@ -238,12 +251,28 @@ int emin_timing(emin_ctx *ctx, double *ms, long long *launches, long long *total
  * that first call before any stream capture.  Calls share the array, which
  * keeps the last call's contents (the counters that must start at zero are
  * cleared on every call), so calls that overlap on the GPU race.
- * n > 4,194,304 (= 16,384 blocks of 256 rows) returns EMIN_ERR_ARG.  Row
- * pointers or column indices out of range are skipped and make *dot NaN.
+ * The address is kept for the life of the process, so calls must not
+ * continue after the device's primary context has been reset
+ * (cudaDeviceReset).  n > 4,194,304 (= 16,384 blocks of 256 rows), or, with
+ * n > 0, a NULL array, returns EMIN_ERR_ARG before anything is queued; n = 0
+ * sets *dot = 0.  Row pointers or column indices out of range are skipped
+ * and make *dot NaN.
  */
 int emin_masked_product_noalloc(int n, int nc, const int *A_rowptr, const int *A_col,
                                 const double *A_val, const int *P_rowptr, const int *P_col,
                                 const double *Y, double *out, double *dot, void *stream);
+
+/*
+ * Measurement aid (the paper has no counterpart): the rate of the fused
+ * multiply-add pipe of the current device in double (EMIN_FP64) or float
+ * (EMIN_MIXED), from one launch of independent FMA chains that fills every
+ * SM, timed with CUDA events on `stream` (cudaStream_t, NULL = legacy
+ * default; the call waits for it).  *fma_per_s receives FMAs per second (2
+ * flops each), *ms (may be NULL) the timed launch's duration.  It is the
+ * ceiling against which the FP64 masked products, bound by FP64 arithmetic
+ * on this part, are reported.
+ */
+int emin_fma_rate(int precision, double *fma_per_s, double *ms, void *stream);
 
 /* Sizes of the context: nnz(A), nnz(P) (either may be NULL). */
 int emin_sizes(emin_ctx *ctx, long long *nnz_a, long long *nnz_p);

@@ -9,7 +9,8 @@
 
 ``EminEnergy.apply(A_val, P_val, problem)``
     E = tr(P^T A P) = <P, mask_P(A P)> (Eq. (trace)) with its analytic
-    backward dE/dP = 2 mask_P(A P) (A symmetric), dE/dA = mask_A(P P^T).
+    backward dE/dP = 2 mask_P(A P) (A symmetric), dE/dA = mask_A(P P^T), all
+    three formed by the library (``emin_energy_grad``).
 
 The fixed data of a problem (patterns, P0, B_c) live in an ``EminProblem``.
 Every computation runs in the CUDA library; tensors must be on the device.
@@ -18,7 +19,7 @@ from __future__ import annotations
 
 import torch
 
-from .emin import Context, emin_outer
+from .emin import Context
 
 
 class EminProblem:
@@ -76,14 +77,14 @@ class EminEnergy(torch.autograd.Function):
     def forward(ctx, A_val, P_val, problem):
         c = problem.context(A_val, precision="fp64")
         P = P_val.detach().contiguous().double()
-        AP = c.kprod(P, project=False)
-        ctx.save_for_backward(P, AP)
+        E, _, _ = c.energy_grad(P)
+        ctx.save_for_backward(P)
         ctx.lib = c
-        return torch.dot(P, AP)
+        return torch.tensor(E, dtype=torch.float64, device=P.device)
 
     @staticmethod
     def backward(ctx, gE):
-        P, AP = ctx.saved_tensors
-        dA = emin_outer(ctx.lib.h, P, P) * gE
-        dP = 2.0 * AP * gE
+        (P,) = ctx.saved_tensors
+        _, dP, dA = ctx.lib.energy_grad(P, float(gE), want_energy=False, want_dX=True,
+                                        want_dA=True)
         return dA, dP, None

@@ -1156,6 +1156,39 @@ int emin_outer(emin_ctx *c, const double *U, const double *V, double *out, int o
     return sync(c);
 }
 
+int emin_energy_grad(emin_ctx *c, const double *X, double scale, double *E, double *dE_dX,
+                     double *dE_dAval, int on_device) {
+    if (!c || !X) return EMIN_ERR_ARG;
+    DeviceGuard g(c->device);
+    if (c->sticky == EMIN_ERR_CUDA) return c->sticky;
+    EMIN_TRY(copy_in(c, c->t64a, X, sizeof(double) * c->nnz_p, on_device));
+    if (E || dE_dX) {
+        // mask_P(A X) on the unscaled A in double, with <X, mask_P(A X)>
+        launch_state_reset(c->L, c->aux.st);
+        launch_kprod<double>(c->L, plain_ops64(c), c->t64a, c->t64b, 0, E ? DOT_AUX : DOT_NONE,
+                             c->aux, 0);
+    }
+    if (dE_dX) {
+        launch_axpby(c->L, c->nnz_p, 2.0 * scale, c->t64b, 0.0, c->t64b);
+        EMIN_TRY(check_launch());
+        EMIN_TRY(copy_out(c, dE_dX, c->t64b, sizeof(double) * c->nnz_p, on_device));
+    }
+    if (dE_dAval) {
+        if (!c->tA) EMIN_TRY(dalloc(c, &c->tA, c->nnz_a));
+        launch_outer(c->L, c->n, c->Ap, c->Aj, c->Pp, c->Pj, c->t64a, c->t64a, scale, c->tA,
+                     c->maxrow_p);
+        EMIN_TRY(check_launch());
+        EMIN_TRY(copy_out(c, dE_dAval, c->tA, sizeof(double) * c->nnz_a, on_device));
+    }
+    EMIN_TRY(check_launch());
+    if (E) {
+        EMIN_TRY(read_state(c, c->aux.st));
+        *E = c->hstate->aux;
+        return EMIN_OK;
+    }
+    return sync(c);
+}
+
 }  // extern "C"
 
 namespace {

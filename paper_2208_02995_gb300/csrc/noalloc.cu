@@ -98,7 +98,9 @@ std::mutex g_mu;
 NoAllocScratch *g_scratch[kNoAllocMaxDevices] = {};
 
 // Device address of the scratch array on the current device, looked up once
-// per device (with that device current).
+// per device (with that device current) and kept for the life of the
+// process: a reset of the device's primary context (cudaDeviceReset) frees
+// the array, so calls must not continue across one.
 int scratch_for_current_device(NoAllocScratch **out) {
     int dev = 0;
     if (cudaGetDevice(&dev) != cudaSuccess) {
@@ -128,6 +130,8 @@ extern "C" int emin_masked_product_noalloc(int n, int nc, const int *A_rowptr, c
                                            double *dot, void *stream) {
     using namespace emin;
     if (n < 0 || nc < 0 || !A_rowptr || !P_rowptr || !dot) return EMIN_ERR_ARG;
+    // with rows to process the kernel dereferences every array
+    if (n > 0 && (!A_col || !A_val || !P_col || !Y || !out)) return EMIN_ERR_ARG;
     if ((long long)n > kNoAllocMaxRows) return EMIN_ERR_ARG;  // beyond the scratch size
     NoAllocScratch *scr = nullptr;
     const int st = scratch_for_current_device(&scr);

@@ -39,7 +39,7 @@ SYMBOLS = ("emin_default_opts", "emin_create", "emin_set_values", "emin_reset", 
            "emin_backward_unrolled",
            "emin_stats", "emin_sizes", "emin_strerror", "emin_destroy", "emin_set_timing",
            "emin_timing", "emin_masked_product_noalloc", "emin_last_error",
-           "emin_trim_memory")
+           "emin_trim_memory", "emin_energy_grad", "emin_fma_rate")
 
 
 class emin_opts(ctypes.Structure):
@@ -86,6 +86,8 @@ def lib():
         L.emin_get_p.argtypes = [_VP, _VP, _I]
         L.emin_kprod.argtypes = [_VP, _VP, _VP, _I, _I]
         L.emin_outer.argtypes = [_VP, _VP, _VP, _VP, _I]
+        L.emin_energy_grad.argtypes = [_VP, _VP, _D, ctypes.POINTER(_D), _VP, _VP, _I]
+        L.emin_fma_rate.argtypes = [_I, ctypes.POINTER(_D), ctypes.POINTER(_D), _VP]
         L.emin_backward.argtypes = [_VP, _VP, _VP, _VP, _I, _D, _I, ctypes.POINTER(_I)]
         L.emin_backward_unrolled.argtypes = [_VP, _VP, _I, _VP, _VP, _I]
         L.emin_stats.argtypes = [_VP, _VP, _I, ctypes.POINTER(_I), ctypes.POINTER(_I),
@@ -247,6 +249,35 @@ def emin_outer(h, U, V, out=None):
     return out
 
 
+def emin_energy_grad(h, X, scale=1.0, want_energy=True, want_dX=False, want_dA=False):
+    """(E, dE/dX, dE/dA) for X on P's pattern; each part only when asked
+    (else None).  Gradients are scaled by `scale`; they are CUDA tensors when
+    X is one, else NumPy arrays."""
+    nnza, nnzp = emin_sizes(h)
+    keep = []
+    dev = _is_cuda_tensor(X)
+
+    def new(count):
+        if dev:
+            import torch
+            return torch.empty(count, dtype=torch.float64, device=X.device)
+        return np.empty(count)
+
+    dX = new(nnzp) if want_dX else None
+    dA = new(nnza) if want_dA else None
+    E = _D(0)
+
+    def ptr(a):
+        if a is None:
+            return None
+        return a.data_ptr() if dev else a.ctypes.data
+
+    _check(lib().emin_energy_grad(h, _ptr(X, np.float64, keep), float(scale),
+                                  ctypes.byref(E) if want_energy else None, ptr(dX), ptr(dA),
+                                  int(dev)), "emin_energy_grad")
+    return (E.value if want_energy else None), dX, dA
+
+
 def emin_backward(h, dL_dP, n_rows, k, max_adj_iters=200, adj_tol=0.0, want_A=True, want_B=True):
     """Returns (dL/dA values, dL/dB (n x k), adjoint steps)."""
     nnza, _ = emin_sizes(h)
@@ -326,17 +357,33 @@ def emin_masked_product_noalloc(n, nc, A_rowptr, A_col, A_val, P_rowptr, P_col, 
         stream = torch.cuda.current_stream().cuda_stream
     elif hasattr(stream, "cuda_stream"):
         stream = stream.cuda_stream
-    keep = []
-    args = [_ptr(A_rowptr, np.int32, keep), _ptr(A_col, np.int32, keep),
-            _ptr(A_val, np.float64, keep), _ptr(P_rowptr, np.int32, keep),
-            _ptr(P_col, np.int32, keep), _ptr(Y, np.float64, keep)]
-    for t in (out, dot):
-        if not (_is_cuda_tensor(t) and t.dtype == torch.float64 and t.is_contiguous()):
-            raise ValueError("out and dot must be contiguous float64 CUDA tensors")
-    _check(lib().emin_masked_product_noalloc(int(n), int(nc), *args, out.data_ptr(),
-                                             dot.data_ptr(), stream),
+    # the kernel reads these arrays after the call returns, on the current
+    # device: no host array and no converted temporary may be passed
+    dev = torch.cuda.current_device()
+    named = (("A_rowptr", A_rowptr, torch.int32), ("A_col", A_col, torch.int32),
+             ("A_val", A_val, torch.float64), ("P_rowptr", P_rowptr, torch.int32),
+             ("P_col", P_col, torch.int32), ("Y", Y, torch.float64),
+             ("out", out, torch.float64), ("dot", dot, torch.float64))
+    for name, t, dt in named:
+        if not (_is_cuda_tensor(t) and t.dtype == dt and t.is_contiguous()
+                and t.device.index == dev):
+            raise ValueError(f"{name} must be a contiguous {dt} CUDA tensor on the current "
+                             f"device (cuda:{dev})")
+    ptrs = [t.data_ptr() for _, t, _ in named]
+    _check(lib().emin_masked_product_noalloc(int(n), int(nc), *ptrs, stream),
            "emin_masked_product_noalloc")
     return out, dot
+
+
+def emin_fma_rate(precision="fp64", stream=None):
+    """(FMAs per second, ms of the timed launch) of the current device's FMA
+    pipe in double ("fp64") or float ("mixed")."""
+    if hasattr(stream, "cuda_stream"):
+        stream = stream.cuda_stream
+    rate, ms = _D(0), _D(0)
+    _check(lib().emin_fma_rate({"fp64": EMIN_FP64, "mixed": EMIN_MIXED}[precision],
+                               ctypes.byref(rate), ctypes.byref(ms), stream), "emin_fma_rate")
+    return rate.value, ms.value
 
 
 def emin_destroy(h):
@@ -413,6 +460,9 @@ class Context:
 
     def outer(self, U, V, out=None):
         return emin_outer(self.h, U, V, out)
+
+    def energy_grad(self, X, scale=1.0, want_energy=True, want_dX=False, want_dA=False):
+        return emin_energy_grad(self.h, X, scale, want_energy, want_dX, want_dA)
 
     def backward(self, dL_dP, max_adj_iters=200, adj_tol=0.0):
         return emin_backward(self.h, dL_dP, self.n, self.k, max_adj_iters, adj_tol)
