@@ -51,6 +51,14 @@ SMALL = [
     I.classical(I.poisson2d(40, 2), grow=2),  # pattern grown twice
 ]
 SMALL_IDS = [p.name for p in SMALL]
+# relative Frobenius error of the mixed path's P after 12 iterations, about
+# ten times what a GB300 measured (2.5e-7 .. 1.2e-5)
+MIXED_P_TOL = {
+    "poisson2d_64": 1e-4, "fv3d_21": 3e-6, "fv3d_23": 3e-6, "aniso3d_14": 1.5e-4,
+    "ring1d_1001": 4e-6, "elast3d_7": 3e-6, "elast3d_8": 4e-6, "random_300_60_1_1": 2e-5,
+    "random_200_90_3_2": 3e-5, "random_150_400_2_3": 8e-6, "classical_fv3d_16": 5e-5,
+    "classical_aniso3d_12": 3e-5, "classical_poisson2d_40": 3e-5,
+}
 
 
 @pytest.mark.parametrize("prob", SMALL, ids=SMALL_IDS)
@@ -110,8 +118,9 @@ def test_mixed_iterations_match_oracle(prob):
     assert abs(E - Eref) <= MIXED_E_TOL * abs(Eref)
     assert o.constraint_error(P) <= CONSTRAINT_TOL
     # P itself is only determined to float accuracy along flat energy
-    # directions; the error is reported, with a sanity bound here
-    assert relf(P, ref["P"]) <= 1e-2
+    # directions: bound it at about ten times the error measured on a GB300
+    # for each problem (so that a regression of the float path shows)
+    assert relf(P, ref["P"]) <= MIXED_P_TOL[prob.name], relf(P, ref["P"])
 
 
 def test_resume_equals_single_call():
