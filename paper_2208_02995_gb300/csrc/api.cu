@@ -55,6 +55,12 @@ struct emin_ctx {
     unsigned int *bmap = nullptr;
     int *tile_map = nullptr;
     int ntiles = 0;
+    // staged node-block product (nbs_kernels.cu): plan and the blob of the
+    // context's iteration precision (float in EMIN_MIXED, double in EMIN_FP64)
+    NbsOps nbs;
+    int4 *nbs_hdr = nullptr, *nbs_runs = nullptr, *nbs_fill_pair = nullptr;
+    int2 *nbs_fill_node = nullptr, *nbs_fill_agg = nullptr;
+    uint4 *nbs_blob = nullptr;
     // projected block SGS plan (EMIN_SGS), built once per context
     int sgs_ngroups = 0, sgs_cap = 0, sgs_gmax = 0;
     long long sgs_nf = 0, sgs_nb = 0, sgs_stage32 = 0, sgs_stage64 = 0;
@@ -305,6 +311,10 @@ Ops<double> iter_ops64(const emin_ctx *c) {
                        c->qv64, c->sell_ptr, c->sa64, c->soff, c->smap, c->sw, nullptr, c->boff, c->blen, c->bmap, c->tile_map, c->ntiles,
                        c->maxrow_p, c->lanes};
     o.sgs = sgs_ops<double>(c, c->sgs_fval64, c->sgs_bval64, c->sgs_bfval64, c->sgs_bbval64);
+    if (c->nbs_blob && c->opts.precision == EMIN_FP64) {
+        o.nbs = c->nbs;
+        o.nbs_blob = reinterpret_cast<const double *>(c->nbs_blob);
+    }
     return o;
 }
 
@@ -313,7 +323,62 @@ Ops<float> iter_ops32(const emin_ctx *c) {
                       c->qv32, c->sell_ptr, c->sa32, c->soff, c->smap, c->sw, c->spk32, c->boff, c->blen, c->bmap, c->tile_map, c->ntiles,
                       c->maxrow_p, c->lanes};
     o.sgs = sgs_ops<float>(c, c->sgs_fval32, c->sgs_bval32, c->sgs_bfval32, c->sgs_bbval32);
+    if (c->nbs_blob && c->opts.precision == EMIN_MIXED) {
+        o.nbs = c->nbs;
+        o.nbs_blob = reinterpret_cast<const float *>(c->nbs_blob);
+    }
     return o;
+}
+
+template <class T>
+int upload(emin_ctx *c, T **dst, const std::vector<T> &src);
+
+// values of the staged product's blob (A^, Ginv, B_c) for the current set-up
+void fill_nbs(emin_ctx *c) {
+    if (!c->nbs_blob) return;
+    if (c->opts.precision == EMIN_MIXED)
+        launch_nbs_fill<float>(c->L, c->nbs, c->Ap, c->Aj, c->Av, c->dsq, c->Ginv, c->Bc,
+                               reinterpret_cast<float *>(c->nbs_blob));
+    else
+        launch_nbs_fill<double>(c->L, c->nbs, c->Ap, c->Aj, c->Av, c->dsq, c->Ginv, c->Bc,
+                                reinterpret_cast<double *>(c->nbs_blob));
+}
+
+// The staged node-block plan from host copies of both patterns (host code,
+// once per context); the problem keeps the node-block product if it does not
+// fit the scheme or the staged kernel cannot launch
+int build_nbs(emin_ctx *c, const int *hAp, const int *hAj, const int *hPp, const int *hPj) {
+    // float (EMIN_MIXED) only: the FP64 product is bound by the FP64 pipe, and
+    // the node-block kernel, which skips a neighbour that does not hold the
+    // lane's aggregate, issues fewer FP64 instructions than the staged one
+    if (c->opts.precision != EMIN_MIXED) return EMIN_OK;
+    const int esize = 4;
+    NbsHost h;
+    // 4 warps and about 100 KB of blob and staged rows per tile (two CTAs per SM)
+    const long long budget = 100 * 1024;
+    if (build_nbs_plan(c->n, hAp, hAj, hPp, hPj, esize, 4, budget, h) != EMIN_OK) return EMIN_OK;
+    NbsOps nb;
+    nb.ntiles = h.ntiles;
+    nb.W = h.W;
+    nb.stage_cap16 = h.stage_cap16;
+    nb.per_sm = esize == 4 ? nbs_prepare<float>(nb) : nbs_prepare<double>(nb);
+    if (nb.per_sm <= 0) return EMIN_OK;
+    EMIN_TRY(upload(c, &c->nbs_hdr, h.hdr));
+    EMIN_TRY(upload(c, &c->nbs_runs, h.runs));
+    EMIN_TRY(upload(c, &c->nbs_fill_pair, h.fill_pair));
+    EMIN_TRY(upload(c, &c->nbs_fill_node, h.fill_node));
+    EMIN_TRY(upload(c, &c->nbs_fill_agg, h.fill_agg));
+    EMIN_TRY(upload(c, &c->nbs_blob, h.blob));
+    nb.hdr = c->nbs_hdr;
+    nb.runs = c->nbs_runs;
+    nb.fill_pair = c->nbs_fill_pair;
+    nb.fill_node = c->nbs_fill_node;
+    nb.fill_agg = c->nbs_fill_agg;
+    nb.nfill_pair = (long long)h.fill_pair.size();
+    nb.nfill_node = (long long)h.fill_node.size();
+    nb.nfill_agg = (long long)h.fill_agg.size();
+    c->nbs = nb;
+    return sync(c);  // the host vectors must outlive the transfers
 }
 
 template <class T>
@@ -506,6 +571,7 @@ int run_setup(emin_ctx *c) {
     launch_diag_scales(L, c->n, c->dinv, c->dsq, c->dhalf);
     launch_gram(L, c->n, c->k, c->Pp, c->Pj, c->Bc, c->Ginv, c->Ginv32, c->opts.rank_policy,
                 c->dint, c->dint + 2);
+    fill_nbs(c);
     launch_restore(L, c->n, c->k, c->Pp, c->Pj, c->Bc, c->B, c->Ginv, c->P0_in, nullptr, nullptr,
                    nullptr, 1, c->P0);
     c->have64 = false;
@@ -774,6 +840,29 @@ int create_impl(emin_ctx *c, const int *A_rowptr, const int *A_col, const double
                                                          cudaMemcpyHostToDevice, c->stream)));
                     EMIN_TRY(sync(c));
                 }
+                // the staged product, from host copies of both patterns
+                std::vector<int> hAp, hAj, hPp, hPj;
+                const int *pAp = A_rowptr, *pAj = A_col, *pPp = P_rowptr, *pPj = P_col;
+                if (on_dev) {
+                    hAp.resize(n + 1);
+                    hAj.resize(c->nnz_a);
+                    hPp.resize(n + 1);
+                    hPj.resize(c->nnz_p);
+                    EMIN_TRY(cuda_status(cudaMemcpyAsync(hAp.data(), c->Ap, sizeof(int) * (n + 1),
+                                                         cudaMemcpyDeviceToHost, c->stream)));
+                    EMIN_TRY(cuda_status(cudaMemcpyAsync(hAj.data(), c->Aj, sizeof(int) * c->nnz_a,
+                                                         cudaMemcpyDeviceToHost, c->stream)));
+                    EMIN_TRY(cuda_status(cudaMemcpyAsync(hPp.data(), c->Pp, sizeof(int) * (n + 1),
+                                                         cudaMemcpyDeviceToHost, c->stream)));
+                    EMIN_TRY(cuda_status(cudaMemcpyAsync(hPj.data(), c->Pj, sizeof(int) * c->nnz_p,
+                                                         cudaMemcpyDeviceToHost, c->stream)));
+                    EMIN_TRY(sync(c));
+                    pAp = hAp.data();
+                    pAj = hAj.data();
+                    pPp = hPp.data();
+                    pPj = hPj.data();
+                }
+                EMIN_TRY(build_nbs(c, pAp, pAj, pPp, pPj));
             }
         }
     }

@@ -515,6 +515,10 @@ void launch_kprod_blk(const Launch &L, const Ops<T> &o, const T *Y, T *out, int 
                       int dot_mode, Work<T> &w, int check_stop) {
     const int nn = o.n / NB;
     if (nn <= 0) return;
+    if (o.nbs.ntiles > 0 && o.nbs_blob) {
+        launch_kprod_nbs<T>(L, o.nbs, o.nbs_blob, Y, out, project, dot_mode, w, check_stop);
+        return;
+    }
     if (o.tile_map && o.ntiles > 0) {
         // register caps without spills: 80 per thread (float), 128 (double)
         launch_blk2<T, sizeof(T) == 4 ? 3 : 2>(L, o, Y, out, project, dot_mode, w, check_stop);

@@ -116,6 +116,27 @@ struct SgsOps {
     const T *fval = nullptr, *bval = nullptr;
 };
 
+// The staged node-block product (nbs_kernels.cu): tiles of whole nodes, per
+// tile two int4 headers ({blob offset16, blob len16, first run, runs},
+// {pairs, nodes, aggregates, Y len16}), the runs of rows of Y to stage
+// ({src16, len16, dst16, 0}, in 16-byte units of Y and of the staging area),
+// and the fill lists that put the values of A^, Ginv and B_c into the blob
+// at every set-up.
+struct NbsOps {
+    int ntiles = 0, W = 0, stage_cap16 = 0, per_sm = 0;  // largest tile: blob + zero block + Y
+    const int4 *hdr = nullptr, *runs = nullptr;
+    const int4 *fill_pair = nullptr;
+    const int2 *fill_node = nullptr, *fill_agg = nullptr;
+    long long nfill_pair = 0, nfill_node = 0, nfill_agg = 0;
+};
+
+struct NbsHost {
+    int W = 4, ntiles = 0, esize = 4, stage_cap16 = 0;
+    std::vector<int4> hdr, runs, fill_pair;
+    std::vector<int2> fill_node, fill_agg;
+    std::vector<uint4> blob;  // static records (values zero)
+};
+
 // Everything a masked-product launch needs to know about the problem.
 // Av is either A itself (plain products: energy, adjoint right-hand sides)
 // or the symmetrically scaled A^ = D^{-1/2} A D^{-1/2} the iteration runs
@@ -153,6 +174,8 @@ struct Ops {
     int maxrow;                   // longest row of P
     int lanes;                    // lanes per row of the row kernels (1 or 32)
     SgsOps<T> sgs;                // projected block SGS (ngroups 0: Jacobi)
+    NbsOps nbs;                   // staged node-block product (ntiles 0: none)
+    const T *nbs_blob = nullptr;  // its blob in this precision (null: not formed)
 };
 
 struct Launch {
@@ -300,6 +323,23 @@ void launch_node_slots(const Launch &L, int n, const int *Pp, int *na);
 template <class T>
 void launch_kprod_blk(const Launch &L, const Ops<T> &o, const T *Y, T *out, int project,
                       int dot_mode, Work<T> &w, int check_stop);
+
+// ---- staged node-block product (nbs_kernels.cu) ----
+// tiles of at most W warps and `budget` bytes of blob plus staged rows of Y;
+// esize = sizeof(T) of the precision the blob is built for.  EMIN_ERR_ARG if
+// the problem does not fit the scheme (then the node-block product serves).
+int build_nbs_plan(int n, const int *Ap, const int *Aj, const int *Pp, const int *Pj, int esize,
+                   int W, long long budget, NbsHost &h);
+long long tile_len16_host(int esize, int W, int npairs, int nnodes, int naggs);
+template <class T>
+void launch_nbs_fill(const Launch &L, const NbsOps &nb, const int *Ap, const int *Aj,
+                     const double *Av, const double *dsq, const double *Ginv, const double *Bc,
+                     T *blob);
+template <class T>
+int nbs_prepare(const NbsOps &nb);
+template <class T>
+void launch_kprod_nbs(const Launch &L, const NbsOps &nb, const T *blob, const T *Y, T *out,
+                      int project, int dot_mode, Work<T> &w, int check_stop);
 
 // ---- adjoint kernels (adjoint_kernels.cu) ----
 void launch_outer(const Launch &L, int n, const int *Ap, const int *Aj, const int *Pp,
