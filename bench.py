@@ -107,12 +107,14 @@ NOMINAL_HBM_GBS = 8000.0  # GB300 HBM3e, nominal (the measured copy rate is the 
 
 def kprod_bytes(prob, vbytes: int) -> int:
     """A (values + column indices + row pointers), P's pattern, Y read once,
-    Y_ written once, the per-row inverse Gram factor and B_c."""
+    Y_ written once (vbytes each), and the fused projection's per-row
+    factor of the Gram matrix and B_c in double (the method's factors are
+    FP64 in both precisions)."""
     n, k = prob.n, prob.k
     a = prob.nnz_a * (vbytes + 4) + 4 * (n + 1)
     pat = 4 * prob.nnz_p + 4 * (n + 1)
     vec = 2 * vbytes * prob.nnz_p
-    fac = n * (k * (k + 1) // 2) * vbytes + prob.nc * k * vbytes
+    fac = n * (k * (k + 1) // 2) * 8 + prob.nc * k * 8
     return a + pat + vec + fac
 
 

@@ -80,7 +80,12 @@ typedef struct {
                       /* EMIN_RANK_PINV: pseudo-inverse of that row's Gram     */
                       /* matrix (the SVD branch of Algorithm 2), counted in    */
                       /* emin_stats                                            */
-    int checks;       /* reserved (0)                                          */
+    int checks;       /* 1: bounds checks in the kernels that gather through  */
+                      /* the plan (masked products, SGS sweeps, plan builds): */
+                      /* an index outside its array is not dereferenced, and  */
+                      /* the call returns EMIN_ERR_PATTERN (sticky); results  */
+                      /* are otherwise bit-identical to checks = 0, which     */
+                      /* runs unchecked kernels (the default)                 */
     void *stream;     /* cudaStream_t; NULL = legacy default stream            */
 } emin_opts;
 

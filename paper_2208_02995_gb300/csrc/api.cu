@@ -90,6 +90,7 @@ struct emin_ctx {
     double *unr_ghat = nullptr, *unr_dext = nullptr, *unr_gA = nullptr;
     float *t32a = nullptr, *t32b = nullptr;
     int *dint = nullptr;       // [0] flags, [1] longest row of P, [2] rank-deficient rows
+    int *chkw = nullptr;       // bounds-check word (emin_opts.checks), never cleared
     DevState *hstate = nullptr;  // pinned mirror
     int *hint = nullptr;         // pinned mirror of dint
     int applied_seen = 0;
@@ -120,6 +121,8 @@ namespace {
 
 thread_local char g_last_error[256] = "";
 
+int with_checks(emin_ctx *c, int st);  // below: the bounds-check word after a call
+
 struct DeviceGuard {
     int prev = -1;
     explicit DeviceGuard(int dev) {
@@ -143,6 +146,7 @@ cudaMemPool_t g_pools[kMaxDevices] = {};
 std::vector<void *> g_host_blocks;  // recycled pinned blocks (kHostBlock bytes)
 constexpr size_t kHostBlock = 256;
 constexpr size_t kHintOffset = 128;
+constexpr int kHintChk = 8;  // the mirror of the check word: hint[kHintChk]
 static_assert(sizeof(DevState) <= kHintOffset, "state mirror overlaps the flag mirror");
 
 cudaMemPool_t device_pool(int dev) {
@@ -270,10 +274,23 @@ int copy_out(emin_ctx *c, void *dst, const void *src, size_t bytes, int on_devic
 int sync(emin_ctx *c) { return cuda_status(cudaStreamSynchronize(c->stream)); }
 
 // masked products on the unscaled A (energy, adjoint right-hand sides)
+// bounds checks of the kernels (emin_opts.checks)
+template <class T>
+void set_checks(const emin_ctx *c, Ops<T> &o) {
+    o.nnz_p = c->nnz_p;
+    o.sgs.ny = c->nnz_p;
+    if (c->opts.checks && c->chkw) {
+        o.chk = c->chkw;
+        o.sgs.chk = c->chkw;
+    }
+}
+
 Ops<double> plain_ops64(const emin_ctx *c) {
-    return Ops<double>{c->n, c->nc, c->k, c->Ap, c->Aj, c->Av, c->Pp, c->Pj, c->Bc, c->Ginv,
-                       nullptr, nullptr, nullptr, nullptr, nullptr, nullptr, nullptr, c->boff, c->blen, c->bmap, c->tile_map, c->ntiles,
-                       c->maxrow_p, c->lanes};
+    Ops<double> o{c->n, c->nc, c->k, c->Ap, c->Aj, c->Av, c->Pp, c->Pj, c->Bc, c->Ginv,
+                  nullptr, nullptr, nullptr, nullptr, nullptr, nullptr, nullptr, c->boff, c->blen, c->bmap, c->tile_map, c->ntiles,
+                  c->maxrow_p, c->lanes};
+    set_checks(c, o);
+    return o;
 }
 
 // the SGS plan with the values of one precision (an empty plan: Jacobi)
@@ -315,6 +332,7 @@ Ops<double> iter_ops64(const emin_ctx *c) {
         o.nbs = c->nbs;
         o.nbs_blob = reinterpret_cast<const double *>(c->nbs_blob);
     }
+    set_checks(c, o);
     return o;
 }
 
@@ -327,6 +345,7 @@ Ops<float> iter_ops32(const emin_ctx *c) {
         o.nbs = c->nbs;
         o.nbs_blob = reinterpret_cast<const float *>(c->nbs_blob);
     }
+    set_checks(c, o);
     return o;
 }
 
@@ -361,6 +380,7 @@ int build_nbs(emin_ctx *c, const int *hAp, const int *hAj, const int *hPp, const
     nb.ntiles = h.ntiles;
     nb.W = h.W;
     nb.stage_cap16 = h.stage_cap16;
+    nb.blob16 = (long long)h.blob.size();
     nb.per_sm = esize == 4 ? nbs_prepare<float>(nb) : nbs_prepare<double>(nb);
     if (nb.per_sm <= 0) return EMIN_OK;
     EMIN_TRY(upload(c, &c->nbs_hdr, h.hdr));
@@ -679,6 +699,10 @@ int create_impl(emin_ctx *c, const int *A_rowptr, const int *A_col, const double
     EMIN_TRY(dalloc(c, &c->dhalf, n));
     EMIN_TRY(dalloc(c, &c->rn, n));
     EMIN_TRY(dalloc(c, &c->dint, 4));
+    if (c->opts.checks) {
+        EMIN_TRY(dalloc(c, &c->chkw, 1));
+        EMIN_TRY(cuda_status(cudaMemsetAsync(c->chkw, 0, sizeof(int), c->stream)));
+    }
     EMIN_TRY(dalloc(c, &c->t64a, c->nnz_p));
     EMIN_TRY(dalloc(c, &c->t64b, c->nnz_p));
     EMIN_TRY(dalloc(c, &c->t64c, c->nnz_p));
@@ -778,7 +802,7 @@ int create_impl(emin_ctx *c, const int *A_rowptr, const int *A_col, const double
         EMIN_TRY(dalloc(c, &c->dpos, n));
         EMIN_TRY(cuda_status(cudaMemsetAsync(c->dint + 3, 0, sizeof(int), c->stream)));
         launch_sell_plan(c->L, n, c->Ap, c->Aj, c->Pp, c->Pj, c->sell_ptr, c->soff, c->smap,
-                         c->sw, c->dint + 3, c->dpos);
+                         c->sw, c->dint + 3, c->dpos, acc, c->opts.checks ? c->chkw : nullptr);
         EMIN_TRY(cuda_status(cudaMemcpyAsync(c->hint + 3, c->dint + 3, sizeof(int),
                                              cudaMemcpyDeviceToHost, c->stream)));
         EMIN_TRY(sync(c));  // the host copy of the offsets must outlive the transfer
@@ -810,7 +834,8 @@ int create_impl(emin_ctx *c, const int *A_rowptr, const int *A_col, const double
                 EMIN_TRY(dalloc(c, &c->boff, ne));
                 EMIN_TRY(dalloc(c, &c->blen, ne));
                 EMIN_TRY(dalloc(c, &c->bmap, ne));
-                launch_block_plan(c->L, n, c->Ap, c->Aj, c->Pp, c->Pj, c->boff, c->blen, c->bmap);
+                launch_block_plan(c->L, n, c->Ap, c->Aj, c->Pp, c->Pj, c->boff, c->blen, c->bmap,
+                                  ne, c->opts.checks ? c->chkw : nullptr);
                 // warp tiles of output blocks: whole nodes per warp, packed greedily
                 const int nn = n / 3;
                 int *dna = nullptr;
@@ -880,7 +905,8 @@ int create_impl(emin_ctx *c, const int *A_rowptr, const int *A_col, const double
     launch_check_finite(c->L, c->B, nk, c->dint);
     launch_check_finite(c->L, c->Bc, nck, c->dint);
     EMIN_TRY(check_launch());
-    return read_flags(c);
+    EMIN_TRY(read_flags(c));
+    return with_checks(c, EMIN_OK);
 }
 
 // The launches of n_iters iterations of Algorithm 3 (scaled variables):
@@ -1092,7 +1118,8 @@ int emin_create(emin_ctx **out, int n, int nc, int k, const int *A_rowptr, const
     if (opts) o = *opts;
     if ((o.precision != EMIN_FP64 && o.precision != EMIN_MIXED) ||
         (o.precond != EMIN_JACOBI && o.precond != EMIN_SGS) ||
-        (o.rank_policy != EMIN_RANK_STRICT && o.rank_policy != EMIN_RANK_PINV))
+        (o.rank_policy != EMIN_RANK_STRICT && o.rank_policy != EMIN_RANK_PINV) ||
+        (o.checks != 0 && o.checks != 1))
         return EMIN_ERR_ARG;
     emin_ctx *c = new (std::nothrow) emin_ctx();
     if (!c) return EMIN_ERR_NOMEM;
@@ -1139,7 +1166,7 @@ int emin_create(emin_ctx **out, int n, int nc, int k, const int *A_rowptr, const
     return EMIN_OK;
 }
 
-int emin_reset(emin_ctx *c) {
+static int call_reset(emin_ctx *c) {
     if (!c) return EMIN_ERR_ARG;
     DeviceGuard g(c->device);
     if (c->sticky == EMIN_ERR_CUDA) return c->sticky;
@@ -1147,7 +1174,7 @@ int emin_reset(emin_ctx *c) {
     return run_setup(c);
 }
 
-int emin_set_values(emin_ctx *c, const double *A_val, const double *B, const double *P0_val,
+static int call_set_values(emin_ctx *c, const double *A_val, const double *B, const double *P0_val,
                     int on_device) {
     if (!c) return EMIN_ERR_ARG;
     DeviceGuard g(c->device);
@@ -1167,7 +1194,7 @@ int emin_set_values(emin_ctx *c, const double *A_val, const double *B, const dou
     return read_flags(c);
 }
 
-int emin_iterate(emin_ctx *c, int n_iters, double tol, int *iters_done, double *rel_dE_last) {
+static int call_iterate(emin_ctx *c, int n_iters, double tol, int *iters_done, double *rel_dE_last) {
     if (!c || n_iters < 0 || !(tol >= 0)) return EMIN_ERR_ARG;
     DeviceGuard g(c->device);
     if (iters_done) *iters_done = 0;
@@ -1192,7 +1219,7 @@ int emin_iterate(emin_ctx *c, int n_iters, double tol, int *iters_done, double *
     return EMIN_OK;
 }
 
-int emin_get_p(emin_ctx *c, double *P_out, int out_on_device) {
+static int call_get_p(emin_ctx *c, double *P_out, int out_on_device) {
     if (!c) return EMIN_ERR_ARG;
     DeviceGuard g(c->device);
     if (c->sticky != EMIN_OK) return c->sticky;
@@ -1201,7 +1228,7 @@ int emin_get_p(emin_ctx *c, double *P_out, int out_on_device) {
     return sync(c);
 }
 
-int emin_energy(emin_ctx *c, double *E) {
+static int call_energy(emin_ctx *c, double *E) {
     if (!c || !E) return EMIN_ERR_ARG;
     DeviceGuard g(c->device);
     if (c->sticky != EMIN_OK) return c->sticky;
@@ -1214,7 +1241,7 @@ int emin_energy(emin_ctx *c, double *E) {
     return EMIN_OK;
 }
 
-int emin_kprod(emin_ctx *c, const double *X, double *out, int project, int on_device) {
+static int call_kprod(emin_ctx *c, const double *X, double *out, int project, int on_device) {
     if (!c) return EMIN_ERR_ARG;
     DeviceGuard g(c->device);
     // the iteration's kernel on x~ = D^{1/2} X, scaled back: y = D^{1/2} y~
@@ -1233,7 +1260,7 @@ int emin_kprod(emin_ctx *c, const double *X, double *out, int project, int on_de
     return sync(c);
 }
 
-int emin_outer(emin_ctx *c, const double *U, const double *V, double *out, int on_device) {
+static int call_outer(emin_ctx *c, const double *U, const double *V, double *out, int on_device) {
     if (!c) return EMIN_ERR_ARG;
     DeviceGuard g(c->device);
     if (!c->tA) EMIN_TRY(dalloc(c, &c->tA, c->nnz_a));
@@ -1245,7 +1272,7 @@ int emin_outer(emin_ctx *c, const double *U, const double *V, double *out, int o
     return sync(c);
 }
 
-int emin_energy_grad(emin_ctx *c, const double *X, double scale, double *E, double *dE_dX,
+static int call_energy_grad(emin_ctx *c, const double *X, double scale, double *E, double *dE_dX,
                      double *dE_dAval, int on_device) {
     if (!c || !X) return EMIN_ERR_ARG;
     DeviceGuard g(c->device);
@@ -1437,7 +1464,7 @@ int unrolled_backward(emin_ctx *c, const double *dLdP, int n_iters, double *gA, 
 
 extern "C" {
 
-int emin_backward_unrolled(emin_ctx *c, const double *dL_dP, int n_iters, double *dL_dAval,
+static int call_backward_unrolled(emin_ctx *c, const double *dL_dP, int n_iters, double *dL_dAval,
                            double *dL_dB, int on_device) {
     if (!c || !dL_dP || n_iters < 1) return EMIN_ERR_ARG;
     DeviceGuard g(c->device);
@@ -1470,7 +1497,7 @@ int emin_backward_unrolled(emin_ctx *c, const double *dL_dP, int n_iters, double
     return sync(c);
 }
 
-int emin_backward(emin_ctx *c, const double *dL_dP, double *dL_dAval, double *dL_dB,
+static int call_backward(emin_ctx *c, const double *dL_dP, double *dL_dAval, double *dL_dB,
                   int max_adj_iters, double adj_tol, int on_device, int *adj_iters) {
     if (!c || !dL_dP || max_adj_iters < 0 || !(adj_tol >= 0)) return EMIN_ERR_ARG;
     DeviceGuard g(c->device);
@@ -1572,6 +1599,65 @@ int emin_sizes(emin_ctx *c, long long *nnz_a, long long *nnz_p) {
     if (nnz_a) *nnz_a = c->nnz_a;
     if (nnz_p) *nnz_p = c->nnz_p;
     return EMIN_OK;
+}
+
+}  // extern "C"
+
+// ---------------------------------------------------------------------------
+// With emin_opts.checks the gather kernels bound-check their indices and OR a
+// fault into the context's check word; every call below reads the word after
+// its work and reports a fault as EMIN_ERR_PATTERN (sticky: the context's
+// later calls report it too).
+// ---------------------------------------------------------------------------
+namespace {
+int with_checks(emin_ctx *c, int st) {
+    if (!c || st != EMIN_OK || !c->opts.checks || !c->chkw) return st;
+    int *hw = c->hint + kHintChk;
+    EMIN_TRY(cuda_status(cudaMemcpyAsync(hw, c->chkw, sizeof(int), cudaMemcpyDeviceToHost,
+                                         c->stream)));
+    EMIN_TRY(sync(c));
+    if (*hw != 0) {
+        std::snprintf(g_last_error, sizeof(g_last_error),
+                      "bounds check: a kernel index fell outside its array (plan or input fault)");
+        c->sticky = EMIN_ERR_PATTERN;
+        return EMIN_ERR_PATTERN;
+    }
+    return EMIN_OK;
+}
+}  // namespace
+
+extern "C" {
+
+int emin_reset(emin_ctx *c) { return with_checks(c, call_reset(c)); }
+int emin_set_values(emin_ctx *c, const double *A_val, const double *B, const double *P0_val,
+                    int on_device) {
+    return with_checks(c, call_set_values(c, A_val, B, P0_val, on_device));
+}
+int emin_iterate(emin_ctx *c, int n_iters, double tol, int *iters_done, double *rel_dE_last) {
+    return with_checks(c, call_iterate(c, n_iters, tol, iters_done, rel_dE_last));
+}
+int emin_get_p(emin_ctx *c, double *P_out, int out_on_device) {
+    return with_checks(c, call_get_p(c, P_out, out_on_device));
+}
+int emin_energy(emin_ctx *c, double *E) { return with_checks(c, call_energy(c, E)); }
+int emin_kprod(emin_ctx *c, const double *X, double *out, int project, int on_device) {
+    return with_checks(c, call_kprod(c, X, out, project, on_device));
+}
+int emin_outer(emin_ctx *c, const double *U, const double *V, double *out, int on_device) {
+    return with_checks(c, call_outer(c, U, V, out, on_device));
+}
+int emin_energy_grad(emin_ctx *c, const double *X, double scale, double *E, double *dE_dX,
+                     double *dE_dAval, int on_device) {
+    return with_checks(c, call_energy_grad(c, X, scale, E, dE_dX, dE_dAval, on_device));
+}
+int emin_backward_unrolled(emin_ctx *c, const double *dL_dP, int n_iters, double *dL_dAval,
+                           double *dL_dB, int on_device) {
+    return with_checks(c, call_backward_unrolled(c, dL_dP, n_iters, dL_dAval, dL_dB, on_device));
+}
+int emin_backward(emin_ctx *c, const double *dL_dP, double *dL_dAval, double *dL_dB,
+                  int max_adj_iters, double adj_tol, int on_device, int *adj_iters) {
+    return with_checks(c, call_backward(c, dL_dP, dL_dAval, dL_dB, max_adj_iters, adj_tol,
+                                        on_device, adj_iters));
 }
 
 }  // extern "C"

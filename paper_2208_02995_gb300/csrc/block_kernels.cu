@@ -75,13 +75,21 @@ __global__ void k_detect_blocks(int nn, const int *__restrict__ Ap, const int *_
 // aggregate slot s of v the slot q of that aggregate in b (15 = none).
 __global__ void k_block_plan(int nn, const int *__restrict__ Ap, const int *__restrict__ Aj,
                              const int *__restrict__ Pp, const int *__restrict__ Pj, int *boff,
-                             unsigned short *blen, unsigned int *bmap) {
+                             unsigned short *blen, unsigned int *bmap, long long nentries,
+                             int *chk) {
+    // chk (bounds checks on): every entry written lies in the plan and every
+    // neighbour node in [0, nn); a violation is skipped and flagged
+    int bad = 0;
     for (int v = blockIdx.x * blockDim.x + threadIdx.x; v < nn; v += gridDim.x * blockDim.x) {
         const int a0 = Ap[NB * v], deg = (Ap[NB * v + 1] - a0) / NB;
         const int p0 = Pp[NB * v], na = (Pp[NB * v + 1] - p0) / KB;
         const int ne0 = a0 / NB;  // a0 / (NB*NB) node entries before v, times NB
         for (int j = 0; j < deg; ++j) {
             const int b = Aj[a0 + NB * j] / NB;
+            if (chk && (b < 0 || b >= nn || (long long)(ne0 / NB + j) >= nentries)) {
+                bad = 1;
+                continue;
+            }
             const int q0 = Pp[NB * b], nbq = (Pp[NB * b + 1] - q0) / KB;
             unsigned int map = 0xFFFFFFFFu;
             for (int s = 0; s < na; ++s) {
@@ -95,6 +103,7 @@ __global__ void k_block_plan(int nn, const int *__restrict__ Ap, const int *__re
             bmap[idx] = map;
         }
     }
+    if (chk && __any_sync(0xffffffffu, bad) && (threadIdx.x & 31) == 0) atomicOr(chk, 1);
 }
 
 // ---------------------------------------------------------------------------
@@ -280,7 +289,7 @@ struct Pair<double> {
     using V = double2;
 };
 
-template <class T, int MINB>
+template <class T, int MINB, bool CK = false>
 __global__ void __launch_bounds__(kBlock, MINB)
 k_kprod_blk2(int ntiles, const int *__restrict__ tile_map, const int *__restrict__ Ap,
              const T *__restrict__ Av, const int *__restrict__ Pp, const int *__restrict__ Pj,
@@ -288,8 +297,9 @@ k_kprod_blk2(int ntiles, const int *__restrict__ tile_map, const int *__restrict
              const unsigned int *__restrict__ bmap, const T *__restrict__ Bc,
              const T *__restrict__ Ginv, const T *__restrict__ Y, T *__restrict__ out,
              int project, int dot_mode, DevState *st, double *partials, double *hist, int cap,
-             int check_stop) {
+             int check_stop, int *chk, long long ny) {
     if (check_stop && st->stop) return;
+    int bad = 0;
     using V = typename Pair<T>::V;
     constexpr int KK = KB * (KB + 1) / 2;
     constexpr int NW = kBlock / 32;
@@ -329,7 +339,9 @@ k_kprod_blk2(int ntiles, const int *__restrict__ tile_map, const int *__restrict
                 T y[NB][KB];
 #pragma unroll
                 for (int c = 0; c < NB; ++c) {
-                    const V *yp = reinterpret_cast<const V *>(Y + yb + c * yl);
+                    // a row segment of KB values: its first index in [0, ny - KB]
+                    const V *yp = reinterpret_cast<const V *>(
+                        Y + chk_index<CK>(yb + c * yl, ny - KB + 1, bad));
 #pragma unroll
                     for (int h = 0; h < KB / 2; ++h) {
                         const V u = yp[h];
@@ -443,6 +455,7 @@ k_kprod_blk2(int ntiles, const int *__restrict__ tile_map, const int *__restrict
             }
         }
     }
+    chk_report<CK>(bad, chk);
     if (dot_mode) {
         __shared__ double sh[32];
         double bt = block_dot_total(dot, sh);
@@ -472,11 +485,12 @@ int launch_detect_blocks(const Launch &L, int n, int k, const int *Ap, const int
 }
 
 void launch_block_plan(const Launch &L, int n, const int *Ap, const int *Aj, const int *Pp,
-                       const int *Pj, int *boff, unsigned short *blen, unsigned int *bmap) {
+                       const int *Pj, int *boff, unsigned short *blen, unsigned int *bmap,
+                       long long nentries, int *chk) {
     const int nn = n / NB;
     if (nn <= 0) return;
     k_block_plan<<<grid_for(nn, L.grid_rows), kBlock, 0, L.stream>>>(nn, Ap, Aj, Pp, Pj, boff, blen,
-                                                                    bmap);
+                                                                    bmap, nentries, chk);
     note_launch();
 }
 
@@ -494,7 +508,7 @@ void launch_blk2(const Launch &L, const Ops<T> &o, const T *Y, T *out, int proje
                  Work<T> &w, int check_stop) {
     static const int per_sm = [] {
         int nb = 0;
-        if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&nb, k_kprod_blk2<T, MINB>, kBlock, 0) !=
+        if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&nb, k_kprod_blk2<T, MINB, false>, kBlock, 0) !=
             cudaSuccess) {
             cudaGetLastError();
             nb = 1;
@@ -504,10 +518,16 @@ void launch_blk2(const Launch &L, const Ops<T> &o, const T *Y, T *out, int proje
     long long cap = (long long)L.nsm * per_sm;
     if (cap > kMaxGrid) cap = kMaxGrid;
     const int g = grid_for((long long)o.ntiles * 32, (int)cap);
-    k_kprod_blk2<T, MINB><<<g, kBlock, 0, L.stream>>>(o.ntiles, o.tile_map, o.Ap, o.Av, o.Pp, o.Pj,
-                                                       o.boff, o.blen, o.bmap, o.Bc, o.Ginv, Y, out,
-                                                       project, dot_mode, w.st, w.partials, w.hist,
-                                                       w.hist_cap, check_stop);
+    if (o.chk)
+        k_kprod_blk2<T, MINB, true><<<g, kBlock, 0, L.stream>>>(
+            o.ntiles, o.tile_map, o.Ap, o.Av, o.Pp, o.Pj, o.boff, o.blen, o.bmap, o.Bc, o.Ginv, Y,
+            out, project, dot_mode, w.st, w.partials, w.hist, w.hist_cap, check_stop, o.chk,
+            o.nnz_p);
+    else
+        k_kprod_blk2<T, MINB><<<g, kBlock, 0, L.stream>>>(
+            o.ntiles, o.tile_map, o.Ap, o.Av, o.Pp, o.Pj, o.boff, o.blen, o.bmap, o.Bc, o.Ginv, Y,
+            out, project, dot_mode, w.st, w.partials, w.hist, w.hist_cap, check_stop, nullptr,
+            o.nnz_p);
 }
 
 template <class T>
@@ -516,7 +536,8 @@ void launch_kprod_blk(const Launch &L, const Ops<T> &o, const T *Y, T *out, int 
     const int nn = o.n / NB;
     if (nn <= 0) return;
     if (o.nbs.ntiles > 0 && o.nbs_blob) {
-        launch_kprod_nbs<T>(L, o.nbs, o.nbs_blob, Y, out, project, dot_mode, w, check_stop);
+        launch_kprod_nbs<T>(L, o.nbs, o.nbs_blob, Y, out, project, dot_mode, w, check_stop, o.chk,
+                            o.nnz_p);
         return;
     }
     if (o.tile_map && o.ntiles > 0) {

@@ -152,6 +152,29 @@ __device__ __forceinline__ double rsqrt_newton(double x) {
     return r * __longlong_as_double((long long)(1023 - ex / 2) << 52);
 }
 
+// ---- bounds checks of the gather kernels (emin_opts.checks = 1) ----
+// With CK, an index outside [0, len) is replaced by 0 (a valid position, so
+// the access stays in bounds) and the thread records the fault; chk_report,
+// called by whole warps at the end of a kernel, ORs the warp's faults into
+// the context's check word, which the host reads after the call and reports
+// as EMIN_ERR_PATTERN.  Without CK both compile to nothing.
+template <bool CK>
+__device__ __forceinline__ int chk_index(int i, long long len, int &bad) {
+    if constexpr (CK) {
+        if (i < 0 || (long long)i >= len) {
+            bad = 1;
+            return 0;
+        }
+    }
+    return i;
+}
+template <bool CK>
+__device__ __forceinline__ void chk_report(int bad, int *word) {
+    if constexpr (CK) {
+        if (__any_sync(0xffffffffu, bad) && (threadIdx.x & 31) == 0) atomicOr(word, 1);
+    }
+}
+
 // ---- scalar steps of Algorithm 3, run by one thread after a reduction ----
 
 // After y^T y_ is known: alpha, dE_k = gamma alpha (Eq. (CG_dEa)), the stop

@@ -114,6 +114,8 @@ struct SgsOps {
     const int *hdr = nullptr, *rpos = nullptr;
     const uint4 *blob = nullptr;
     const T *fval = nullptr, *bval = nullptr;
+    int *chk = nullptr;  // bounds checks: the context's check word (null: off)
+    long long ny = 0;    // entries of the vectors on P's pattern
 };
 
 // The staged node-block product (nbs_kernels.cu): tiles of whole nodes, per
@@ -124,6 +126,7 @@ struct SgsOps {
 // at every set-up.
 struct NbsOps {
     int ntiles = 0, W = 0, stage_cap16 = 0, per_sm = 0;  // largest tile: blob + zero block + Y
+    long long blob16 = 0;                                 // 16-byte units of the blob
     const int4 *hdr = nullptr, *runs = nullptr;
     const int4 *fill_pair = nullptr;
     const int2 *fill_node = nullptr, *fill_agg = nullptr;
@@ -176,6 +179,10 @@ struct Ops {
     SgsOps<T> sgs;                // projected block SGS (ngroups 0: Jacobi)
     NbsOps nbs;                   // staged node-block product (ntiles 0: none)
     const T *nbs_blob = nullptr;  // its blob in this precision (null: not formed)
+    // bounds checks (emin_opts.checks): the context's check word, null when off;
+    // nnz_p bounds every gather of a vector on P's pattern
+    int *chk = nullptr;
+    long long nnz_p = 0;
 };
 
 struct Launch {
@@ -239,7 +246,7 @@ void launch_sell_len(const Launch &L, int n, const int *Ap, int *slen);
 // does not fit the packed word
 void launch_sell_plan(const Launch &L, int n, const int *Ap, const int *Aj, const int *Pp,
                       const int *Pj, const int *sell_ptr, int *soff, unsigned short *smap,
-                      unsigned int *sw, int *wide, int *dpos);
+                      unsigned int *sw, int *wide, int *dpos, long long nsell, int *chk);
 // A^ in plan order into sa, or (float, spk non-null) interleaved with the
 // packed words sw into spk; dsq32 (float, may be null): D^{-1/2} as floats
 // (when dsq holds float-exact values), read instead of narrowing dsq
@@ -317,7 +324,8 @@ void launch_loop_control(const Launch &L, DevState *st, cudaGraphConditionalHand
 int launch_detect_blocks(const Launch &L, int n, int k, const int *Ap, const int *Aj,
                          const int *Pp, const int *Pj, int *bad);
 void launch_block_plan(const Launch &L, int n, const int *Ap, const int *Aj, const int *Pp,
-                       const int *Pj, int *boff, unsigned short *blen, unsigned int *bmap);
+                       const int *Pj, int *boff, unsigned short *blen, unsigned int *bmap,
+                       long long nentries, int *chk);
 long long block_plan_entries(long long nnz_a);
 void launch_node_slots(const Launch &L, int n, const int *Pp, int *na);
 template <class T>
@@ -339,7 +347,8 @@ template <class T>
 int nbs_prepare(const NbsOps &nb);
 template <class T>
 void launch_kprod_nbs(const Launch &L, const NbsOps &nb, const T *blob, const T *Y, T *out,
-                      int project, int dot_mode, Work<T> &w, int check_stop);
+                      int project, int dot_mode, Work<T> &w, int check_stop, int *chk,
+                      long long ny);
 
 // ---- adjoint kernels (adjoint_kernels.cu) ----
 void launch_outer(const Launch &L, int n, const int *Ap, const int *Aj, const int *Pp,

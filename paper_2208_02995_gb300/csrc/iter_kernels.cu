@@ -244,27 +244,28 @@ k_project_warp(int n, int k, const int *__restrict__ Pp, const int *__restrict__
 // gathers y_lq for every slot s of row i that row l holds; one FMA per
 // in-pattern product.  Epilogue per row: x -= q (q^T x), store, y^T y_.
 // ---------------------------------------------------------------------------
-template <class T>
+template <bool CK, class T>
 __device__ __forceinline__ void sell_step(T a, int off, unsigned int im, const T *__restrict__ Y,
-                                          T &a0, T &a1, T &a2, T &a3) {
+                                          T &a0, T &a1, T &a2, T &a3, long long ny, int &bad) {
     const unsigned int q0 = im & 7u, q1 = (im >> 3) & 7u, q2 = (im >> 6) & 7u, q3 = (im >> 9) & 7u;
-    if (q0 < 4u) a0 = fmat(a, Y[off + q0], a0);
-    if (q1 < 4u) a1 = fmat(a, Y[off + q1], a1);
-    if (q2 < 4u) a2 = fmat(a, Y[off + q2], a2);
-    if (q3 < 4u) a3 = fmat(a, Y[off + q3], a3);
+    if (q0 < 4u) a0 = fmat(a, Y[chk_index<CK>(off + (int)q0, ny, bad)], a0);
+    if (q1 < 4u) a1 = fmat(a, Y[chk_index<CK>(off + (int)q1, ny, bad)], a1);
+    if (q2 < 4u) a2 = fmat(a, Y[chk_index<CK>(off + (int)q2, ny, bad)], a2);
+    if (q3 < 4u) a3 = fmat(a, Y[chk_index<CK>(off + (int)q3, ny, bad)], a3);
 }
 
 // The first 8 entries of every row are loaded in one round (three coalesced
 // runs per entry) before any gather of Y is issued, so that a slice costs
 // two memory round trips; longer rows continue in a loop.
-template <class T>
+template <class T, bool CK = false>
 __global__ void __launch_bounds__(kBlock)
 k_kprod_k1_sell(int n, const int *__restrict__ sell_ptr, const T *__restrict__ sa,
                 const int *__restrict__ soff, const unsigned short *__restrict__ smap,
                 const int *__restrict__ Pp, const T *__restrict__ qv, const T *__restrict__ Y,
                 T *__restrict__ out, int project, int dot_mode, DevState *st, double *partials,
-                double *hist, int cap, int check_stop) {
+                double *hist, int cap, int check_stop, int *chk, long long ny) {
     if (check_stop && st->stop) return;
+    int bad = 0;
     constexpr int U = 8;
     const int lane = threadIdx.x & 31;
     const int warp = (blockIdx.x * blockDim.x + threadIdx.x) >> 5;
@@ -328,10 +329,10 @@ k_kprod_k1_sell(int n, const int *__restrict__ sell_ptr, const T *__restrict__ s
         }
         T a0 = T(0), a1 = T(0), a2 = T(0), a3 = T(0);
 #pragma unroll
-        for (int j = 0; j < U; ++j) sell_step(av[j], ov[j], mv[j], Y, a0, a1, a2, a3);
+        for (int j = 0; j < U; ++j) sell_step<CK>(av[j], ov[j], mv[j], Y, a0, a1, a2, a3, ny, bad);
         for (int j = U; j < len; ++j)
-            sell_step(__ldcs(pa + j * 32), __ldcs(po + j * 32), (unsigned int)__ldcs(pm + j * 32), Y,
-                      a0, a1, a2, a3);
+            sell_step<CK>(__ldcs(pa + j * 32), __ldcs(po + j * 32), (unsigned int)__ldcs(pm + j * 32),
+                          Y, a0, a1, a2, a3, ny, bad);
         T x[4] = {a0, a1, a2, a3};
         if (project) {
             T t = T(0);
@@ -347,6 +348,7 @@ k_kprod_k1_sell(int n, const int *__restrict__ sell_ptr, const T *__restrict__ s
                 if (dot_mode) dot.add(yown[s], x[s]);
             }
     }
+    chk_report<CK>(bad, chk);
     if (dot_mode) {
         __shared__ double sh[32];
         double bt = block_dot_total(dot, sh);
@@ -378,13 +380,16 @@ __device__ __forceinline__ void cp_async_wait0() { asm volatile("cp.async.wait_g
 constexpr int kStageWarps = kBlock / 32;
 constexpr int kStageCap = kStageWarps * 8 * 32;  // plan entries per buffer
 
+template <bool CK = false>
 __global__ void __launch_bounds__(kBlock)
 k_kprod_k1_staged(int n, const int *__restrict__ sell_ptr, const float *__restrict__ sa,
                   const int *__restrict__ soff, const unsigned short *__restrict__ smap,
                   const int *__restrict__ Pp, const float *__restrict__ qv,
                   const float *__restrict__ Y, float *__restrict__ out, int project, int dot_mode,
-                  DevState *st, double *partials, double *hist, int cap, int check_stop) {
+                  DevState *st, double *partials, double *hist, int cap, int check_stop, int *chk,
+                  long long ny) {
     if (check_stop && st->stop) return;
+    int bad = 0;
     __shared__ __align__(16) float sA[2][kStageCap];
     __shared__ __align__(16) int sO[2][kStageCap];
     __shared__ __align__(16) unsigned short sM[2][kStageCap];
@@ -462,11 +467,13 @@ k_kprod_k1_staged(int n, const int *__restrict__ sell_ptr, const float *__restri
                     }
                 }
 #pragma unroll
-                for (int j = 0; j < 8; ++j) sell_step(av[j], ov[j], mv[j], Y, a0, a1, a2, a3);
+                for (int j = 0; j < 8; ++j)
+                    sell_step<CK>(av[j], ov[j], mv[j], Y, a0, a1, a2, a3, ny, bad);
             } else {
                 for (int j = 0; j < len; ++j)
-                    sell_step(__ldcs(sa + gb + j * 32 + lane), __ldcs(soff + gb + j * 32 + lane),
-                              (unsigned int)__ldcs(smap + gb + j * 32 + lane), Y, a0, a1, a2, a3);
+                    sell_step<CK>(__ldcs(sa + gb + j * 32 + lane), __ldcs(soff + gb + j * 32 + lane),
+                                  (unsigned int)__ldcs(smap + gb + j * 32 + lane), Y, a0, a1, a2,
+                                  a3, ny, bad);
             }
             float x[4] = {a0, a1, a2, a3};
             if (project) {
@@ -486,6 +493,7 @@ k_kprod_k1_staged(int n, const int *__restrict__ sell_ptr, const float *__restri
         __syncthreads();  // buffer b is refilled two groups later
     }
     cp_async_wait0();
+    chk_report<CK>(bad, chk);
     if (dot_mode) {
         __shared__ double sh[32];
         double bt = block_dot_total(dot, sh);
@@ -535,9 +543,10 @@ struct PkPlan<double> {
 // a row of the warp has entries of P, the only case that gets here) and a
 // select keeps its accumulator, so the loads of all L entries issue back to
 // back instead of one divergent branch per slot.
-template <class T, int L, int M>
+template <class T, int L, int M, bool CK>
 __device__ __forceinline__ void pk_entries(const PkPlan<T> &pl, int pos, int p0,
-                                           const T *__restrict__ Y, T *acc) {
+                                           const T *__restrict__ Y, T *acc, long long ny,
+                                           int &bad) {
     T a[L];
     unsigned int w[L];
 #pragma unroll
@@ -549,7 +558,7 @@ __device__ __forceinline__ void pk_entries(const PkPlan<T> &pl, int pos, int p0,
 #pragma unroll
         for (int s = 0; s < M; ++s) {
             const unsigned int q = (w[j] >> (3 * s)) & 7u;
-            v[j][s] = Y[q < 4u ? off + (int)q : 0];
+            v[j][s] = Y[chk_index<CK>(q < 4u ? off + (int)q : 0, ny, bad)];
         }
     }
 #pragma unroll
@@ -561,19 +570,19 @@ __device__ __forceinline__ void pk_entries(const PkPlan<T> &pl, int pos, int p0,
         }
 }
 
-template <class T, int M>
+template <class T, int M, bool CK>
 __device__ __forceinline__ void pk_row(const PkPlan<T> &pl, int pos, int len, int p0,
-                                       const T *__restrict__ Y, T *acc) {
+                                       const T *__restrict__ Y, T *acc, long long ny, int &bad) {
     switch (len) {
-        case 7: pk_entries<T, 7, M>(pl, pos, p0, Y, acc); break;
-        case 6: pk_entries<T, 6, M>(pl, pos, p0, Y, acc); break;
-        case 5: pk_entries<T, 5, M>(pl, pos, p0, Y, acc); break;
-        case 4: pk_entries<T, 4, M>(pl, pos, p0, Y, acc); break;
-        case 8: pk_entries<T, 8, M>(pl, pos, p0, Y, acc); break;
+        case 7: pk_entries<T, 7, M, CK>(pl, pos, p0, Y, acc, ny, bad); break;
+        case 6: pk_entries<T, 6, M, CK>(pl, pos, p0, Y, acc, ny, bad); break;
+        case 5: pk_entries<T, 5, M, CK>(pl, pos, p0, Y, acc, ny, bad); break;
+        case 4: pk_entries<T, 4, M, CK>(pl, pos, p0, Y, acc, ny, bad); break;
+        case 8: pk_entries<T, 8, M, CK>(pl, pos, p0, Y, acc, ny, bad); break;
         default: {
             int j = 0;
-            for (; j + 4 <= len; j += 4) pk_entries<T, 4, M>(pl, pos + 32 * j, p0, Y, acc);
-            for (; j < len; ++j) pk_entries<T, 1, M>(pl, pos + 32 * j, p0, Y, acc);
+            for (; j + 4 <= len; j += 4) pk_entries<T, 4, M, CK>(pl, pos + 32 * j, p0, Y, acc, ny, bad);
+            for (; j < len; ++j) pk_entries<T, 1, M, CK>(pl, pos + 32 * j, p0, Y, acc, ny, bad);
         }
     }
 }
@@ -588,17 +597,18 @@ constexpr int kPkBlock = 512;
 // (y^T y_ -> alpha), DOT_AUX (y^T y_ -> aux), or DOT_START: out = -Pi(A^ x0)
 // with the floor's <r, r> taken before the projection and (gamma0) gamma_0
 // = <r~, r~> after it, reduced together.
-template <class T, int DM>
+template <class T, int DM, bool CK = false>
 __global__ void __launch_bounds__(kPkBlock)
 k_kprod_k1_pk(int n, const int *__restrict__ sell_ptr, PkPlan<T> pl, const int *__restrict__ Pp,
               const T *__restrict__ qv, const T *__restrict__ Y, T *__restrict__ out, int project,
               int gamma0, DevState *st, double *partials, double *hist, int cap,
-              int check_stop) {
+              int check_stop, int *chk, long long ny) {
     constexpr bool dot_mode = (DM == DOT_ALPHA || DM == DOT_AUX);
     Dot<T> dot0, dot1;  // DOT_START: the sums before and after the projection
     if (check_stop && st->stop) return;
     const int lane = threadIdx.x & 31;
     const int nslices = (n + 31) >> 5;
+    int bad = 0;
     Dot<T> dot;
     // the loop is uniform over the warp (one slice per warp and pass)
     for (int sl = (blockIdx.x * blockDim.x + threadIdx.x) >> 5; sl < nslices;
@@ -624,10 +634,10 @@ k_kprod_k1_pk(int n, const int *__restrict__ sell_ptr, PkPlan<T> pl, const int *
         const int pos = base + lane;
         switch (mw) {
             case 0: break;  // no row of the slice has an entry of P
-            case 1: pk_row<T, 1>(pl, pos, len, p0, Y, x); break;
-            case 2: pk_row<T, 2>(pl, pos, len, p0, Y, x); break;
-            case 3: pk_row<T, 3>(pl, pos, len, p0, Y, x); break;
-            default: pk_row<T, 4>(pl, pos, len, p0, Y, x); break;
+            case 1: pk_row<T, 1, CK>(pl, pos, len, p0, Y, x, ny, bad); break;
+            case 2: pk_row<T, 2, CK>(pl, pos, len, p0, Y, x, ny, bad); break;
+            case 3: pk_row<T, 3, CK>(pl, pos, len, p0, Y, x, ny, bad); break;
+            default: pk_row<T, 4, CK>(pl, pos, len, p0, Y, x, ny, bad); break;
         }
         if constexpr (DM == DOT_START) {
 #pragma unroll
@@ -653,6 +663,7 @@ k_kprod_k1_pk(int n, const int *__restrict__ sell_ptr, PkPlan<T> pl, const int *
                 if constexpr (dot_mode) dot.add(yown[s], x[s]);
             }
     }
+    chk_report<CK>(bad, chk);
     if constexpr (dot_mode) {
         __shared__ double sh[32];
         double bt = block_dot_total(dot, sh);
@@ -893,15 +904,19 @@ void launch_kprod(const Launch &L, const Ops<T> &o, const T *Y, T *out, int proj
         const long long need = (warps * 32 + kPkBlock - 1) / kPkBlock;
         // one resident wave of the instantiation that runs (queried at create)
         switch (dot_mode) {
-#define EMIN_PK(DMV)                                                                       \
-    case DMV: {                                                                            \
-        long long cap = (long long)L.nsm * pk_per_sm<T, DMV>();                            \
-        if (cap > kMaxGrid) cap = kMaxGrid;                                                \
-        const int g = (int)(need < cap ? (need > 0 ? need : 1) : cap);                    \
-        k_kprod_k1_pk<T, DMV><<<g, kPkBlock, 0, L.stream>>>(o.n, o.sell_ptr, pl, o.Pp, o.qv, \
-                                                            Y, out, project, 0, w.st,        \
-                                                            w.partials, w.hist, w.hist_cap,  \
-                                                            check_stop);                     \
+#define EMIN_PK(DMV)                                                                         \
+    case DMV: {                                                                              \
+        long long cap = (long long)L.nsm * pk_per_sm<T, DMV>();                              \
+        if (cap > kMaxGrid) cap = kMaxGrid;                                                  \
+        const int g = (int)(need < cap ? (need > 0 ? need : 1) : cap);                      \
+        if (o.chk)                                                                           \
+            k_kprod_k1_pk<T, DMV, true><<<g, kPkBlock, 0, L.stream>>>(                       \
+                o.n, o.sell_ptr, pl, o.Pp, o.qv, Y, out, project, 0, w.st, w.partials,       \
+                w.hist, w.hist_cap, check_stop, o.chk, o.nnz_p);                             \
+        else                                                                                 \
+            k_kprod_k1_pk<T, DMV><<<g, kPkBlock, 0, L.stream>>>(                             \
+                o.n, o.sell_ptr, pl, o.Pp, o.qv, Y, out, project, 0, w.st, w.partials,       \
+                w.hist, w.hist_cap, check_stop, nullptr, o.nnz_p);                           \
     } break;
             EMIN_PK(DOT_NONE)
             EMIN_PK(DOT_ALPHA)
@@ -914,16 +929,24 @@ void launch_kprod(const Launch &L, const Ops<T> &o, const T *Y, T *out, int proj
             // one block per group of 8 slices, at most the resident grid
             const long long groups = ((o.n + 31) / 32 + kStageWarps - 1) / kStageWarps;
             const int g = (int)(groups < L.grid_staged ? groups : L.grid_staged);
-            k_kprod_k1_staged<<<g, kBlock, 0, L.stream>>>(o.n, o.sell_ptr, o.sa, o.soff, o.smap,
-                                                          o.Pp, o.qv, Y, out, project, dot_mode,
-                                                          w.st, w.partials, w.hist, w.hist_cap,
-                                                          check_stop);
+            if (o.chk)
+                k_kprod_k1_staged<true><<<g, kBlock, 0, L.stream>>>(
+                    o.n, o.sell_ptr, o.sa, o.soff, o.smap, o.Pp, o.qv, Y, out, project, dot_mode,
+                    w.st, w.partials, w.hist, w.hist_cap, check_stop, o.chk, o.nnz_p);
+            else
+                k_kprod_k1_staged<<<g, kBlock, 0, L.stream>>>(
+                    o.n, o.sell_ptr, o.sa, o.soff, o.smap, o.Pp, o.qv, Y, out, project, dot_mode,
+                    w.st, w.partials, w.hist, w.hist_cap, check_stop, nullptr, o.nnz_p);
         } else {
             const int g = grid_for((long long)((o.n + 31) / 32) * 32, L.grid_rows);
-            k_kprod_k1_sell<T><<<g, kBlock, 0, L.stream>>>(o.n, o.sell_ptr, o.sa, o.soff, o.smap,
-                                                            o.Pp, o.qv, Y, out, project, dot_mode,
-                                                            w.st, w.partials, w.hist, w.hist_cap,
-                                                            check_stop);
+            if (o.chk)
+                k_kprod_k1_sell<T, true><<<g, kBlock, 0, L.stream>>>(
+                    o.n, o.sell_ptr, o.sa, o.soff, o.smap, o.Pp, o.qv, Y, out, project, dot_mode,
+                    w.st, w.partials, w.hist, w.hist_cap, check_stop, o.chk, o.nnz_p);
+            else
+                k_kprod_k1_sell<T><<<g, kBlock, 0, L.stream>>>(
+                    o.n, o.sell_ptr, o.sa, o.soff, o.smap, o.Pp, o.qv, Y, out, project, dot_mode,
+                    w.st, w.partials, w.hist, w.hist_cap, check_stop, nullptr, o.nnz_p);
         }
     } else if (o.k == 1 && o.maxrow <= 4) {
         k_kprod_row_k1<T, 4><<<grid_for(o.n, L.grid_rows), kBlock, 0, L.stream>>>(
@@ -978,9 +1001,14 @@ bool launch_kprod_start(const Launch &L, const Ops<T> &o, const T *x0, T *R, Wor
     const long long cap = (long long)L.nsm * pk_per_sm<T, DOT_START>();
     int g = (int)(need < cap ? (need > 0 ? need : 1) : cap);
     if (2 * g > kMaxGrid) g = kMaxGrid / 2;  // two partial sums per block
-    k_kprod_k1_pk<T, DOT_START><<<g, kPkBlock, 0, L.stream>>>(
-        o.n, o.sell_ptr, pl, o.Pp, o.qv, x0, R, 1, gamma0, w.st, w.partials, w.hist, w.hist_cap,
-        0);
+    if (o.chk)
+        k_kprod_k1_pk<T, DOT_START, true><<<g, kPkBlock, 0, L.stream>>>(
+            o.n, o.sell_ptr, pl, o.Pp, o.qv, x0, R, 1, gamma0, w.st, w.partials, w.hist,
+            w.hist_cap, 0, o.chk, o.nnz_p);
+    else
+        k_kprod_k1_pk<T, DOT_START><<<g, kPkBlock, 0, L.stream>>>(
+            o.n, o.sell_ptr, pl, o.Pp, o.qv, x0, R, 1, gamma0, w.st, w.partials, w.hist,
+            w.hist_cap, 0, nullptr, o.nnz_p);
     note_launch();
     return true;
 }
@@ -1055,7 +1083,7 @@ void launch_row_scale(const Launch &L, int n, const int *Pp, int lanes, const do
 
 int staged_blocks_per_sm() {
     int nb = 0;
-    if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&nb, k_kprod_k1_staged, kBlock, 0) !=
+    if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&nb, k_kprod_k1_staged<false>, kBlock, 0) !=
         cudaSuccess) {
         cudaGetLastError();
         nb = 1;

@@ -222,17 +222,25 @@ struct PairOf<double> {
 // The staged product.  Dynamic shared memory: [blob cap][Y cap][scratch
 // W*32*19 T]; one mbarrier counts the bytes of a tile's copies.
 // ---------------------------------------------------------------------------
-template <class T, int W>
+template <class T, int W, bool CK = false>
 __global__ void __launch_bounds__(W * 32)
 k_kprod_nbs(int ntiles, const int4 *__restrict__ thdr, const uint4 *__restrict__ blob,
             const int4 *__restrict__ runs, int stage_cap16, const T *__restrict__ Y,
             T *__restrict__ out, int project, int dot_mode, DevState *st, double *partials,
-            double *hist, int cap, int check_stop) {
+            double *hist, int cap, int check_stop, int *chk, long long ny, long long blob16) {
     using V = typename PairOf<T>::V;
     if (check_stop && st->stop) return;
+    int bad = 0;
+    // with checks: copies that would leave the blob, Y (16-byte rounded) or
+    // the staging area are skipped and flagged
+    const long long y16 = (ny * (long long)sizeof(T) + 15) / 16;
+    auto run_ok = [&](const int4 &rn, int blen16) {
+        return rn.x >= 0 && rn.y >= 0 && (long long)rn.x + rn.y <= y16 &&
+               rn.z >= kZero * (int)sizeof(T) / 16 && (long long)blen16 + rn.z + rn.y <= stage_cap16;
+    };
     extern __shared__ __align__(16) unsigned char smem[];
     __shared__ __align__(8) unsigned long long bar;
-    __shared__ int s_abort;
+    __shared__ int s_abort, s_skip;
     unsigned char *sBlob = smem;
     T(*sT)[NB * KB + 1] = reinterpret_cast<T(*)[NB * KB + 1]>(smem + (size_t)stage_cap16 * 16);
     const int tid = threadIdx.x;
@@ -241,6 +249,7 @@ k_kprod_nbs(int ntiles, const int4 *__restrict__ thdr, const uint4 *__restrict__
         fence_mbar_init();
         fence_proxy_async();
         s_abort = 0;
+        s_skip = 0;
     }
     __syncthreads();
     Dot<T> dot;
@@ -252,14 +261,39 @@ k_kprod_nbs(int ntiles, const int4 *__restrict__ thdr, const uint4 *__restrict__
         T *sY = reinterpret_cast<T *>(smem + (size_t)h0.y * 16);
         for (int i = tid; i < kZero; i += W * 32) sY[i] = T(0);
         if (tid < 32) {
+            // with checks, a tile whose header does not describe a blob inside
+            // the blob array and the staging area is skipped whole
+            bool tile_ok = true;
+            if constexpr (CK)
+                tile_ok = h0.x >= 0 && h0.y >= 0 && h1.x >= 0 && h1.y >= 0 && h1.z >= 0 &&
+                          h1.w >= 0 && h0.z >= 0 && h0.w >= 0 &&
+                          (long long)h0.x + h0.y <= blob16 &&
+                          tile_len16<T>(W, h1.x, h1.y, h1.z) == h0.y && h1.y <= W * 32 &&
+                          (long long)h0.y + kZero * (int)sizeof(T) / 16 + h1.w <= stage_cap16;
             if (tid == 0) {
                 fence_proxy_async();  // earlier generic reads of this memory come first
-                mbar_expect_tx(&bar, (unsigned)(h0.y + h1.w) * 16u);
+                unsigned bytes = (unsigned)(h0.y + h1.w) * 16u;
+                if constexpr (CK) {
+                    bytes = 0u;
+                    if (tile_ok) {
+                        bytes = (unsigned)h0.y * 16u;
+                        for (int r = 0; r < h0.w; ++r) {
+                            const int4 rn = runs[h0.z + r];
+                            if (run_ok(rn, h0.y)) bytes += (unsigned)rn.y * 16u;
+                            else bad = 1;
+                        }
+                    } else {
+                        bad = 1;
+                        s_skip = 1;
+                    }
+                }
+                mbar_expect_tx(&bar, bytes);
             }
             __syncwarp();
-            if (tid == 0) bulk_g2s(sBlob, blob + h0.x, (unsigned)h0.y * 16u, &bar);
-            for (int r = tid; r < h0.w; r += 32) {
+            if (tid == 0 && tile_ok) bulk_g2s(sBlob, blob + h0.x, (unsigned)h0.y * 16u, &bar);
+            for (int r = tid; r < (tile_ok ? h0.w : 0); r += 32) {
                 const int4 rn = runs[h0.z + r];  // {src16, len16, dst16}
+                if (CK && !run_ok(rn, h0.y)) continue;
                 bulk_g2s(reinterpret_cast<unsigned char *>(sY) + (size_t)rn.z * 16,
                          reinterpret_cast<const unsigned char *>(Y) + (size_t)rn.x * 16,
                          (unsigned)rn.y * 16u, &bar);
@@ -276,6 +310,12 @@ k_kprod_nbs(int ntiles, const int4 *__restrict__ thdr, const uint4 *__restrict__
         phase ^= 1u;
         __syncthreads();
         if (s_abort) break;
+        if (CK && s_skip) {
+            __syncthreads();  // every thread has read the flag
+            if (tid == 0) s_skip = 0;
+            __syncthreads();
+            continue;
+        }
 
         const TileView tv = tile_view<T>(W, h1.x, h1.y, h1.z);
         const int *sLane = reinterpret_cast<const int *>(sBlob);
@@ -287,11 +327,19 @@ k_kprod_nbs(int ntiles, const int4 *__restrict__ thdr, const uint4 *__restrict__
 
         const int rec = sLane[tid];
         const bool valid = rec >= 0;
-        const int ni = rec & 1023, s = (rec >> 10) & 7, ai = rec >> 13;
+        // (padding lanes, rec = -1, take no entries and index nothing)
+        const int ni = valid ? chk_index<CK>(rec & 1023, h1.y, bad) : 0, s = (rec >> 10) & 7;
+        const int ai = valid ? chk_index<CK>(rec >> 13, h1.z, bad) : 0;
         int4 nd = make_int4(0, 0, 0, 0);
         if (valid) nd = sNode[ni];
-        const int pair0 = nd.x & 0xFFFFF, ng = valid ? (nd.x >> 20) : 0;
+        int pair0 = nd.x & 0xFFFFF, ng = valid ? (nd.x >> 20) : 0;
+        if (CK && (long long)pair0 + ng > h1.x) {
+            bad = 1;
+            pair0 = ng = 0;
+        }
         const int p0 = nd.y, mrow = nd.z & 255, first = tid - s, nslot = (nd.z >> 16) & 255;
+        // the Y area of this tile, in elements (a row segment reads KB of them)
+        const long long ylim = ((long long)stage_cap16 - h0.y) * 16 / (long long)sizeof(T) - KB + 1;
         T acc[NB][KB];
 #pragma unroll
         for (int r = 0; r < NB; ++r)
@@ -313,7 +361,7 @@ k_kprod_nbs(int ntiles, const int4 *__restrict__ thdr, const uint4 *__restrict__
                 const int yb = ok ? (int)(bo & 0x0FFFFFFFu) + KB * (int)q : 0;
                 T y[NB][KB];
 #pragma unroll
-                for (int c = 0; c < NB; ++c) lds_row6(sY + yb + c * yl, y[c]);
+                for (int c = 0; c < NB; ++c) lds_row6(sY + chk_index<CK>(yb + c * yl, ylim, bad), y[c]);
 #pragma unroll
                 for (int r = 0; r < NB; ++r) {
                     const T a0 = h ? a2[r * NB].y : a2[r * NB].x;
@@ -404,8 +452,9 @@ k_kprod_nbs(int ntiles, const int4 *__restrict__ thdr, const uint4 *__restrict__
 #pragma unroll
             for (int r = 0; r < NB; ++r) {
                 const int o = p0 + r * mrow + KB * s;
-                V *op = reinterpret_cast<V *>(out + o);
-                const V *yo = reinterpret_cast<const V *>(sY + own + r * mrow + KB * s);
+                V *op = reinterpret_cast<V *>(out + chk_index<CK>(o, ny - KB + 1, bad));
+                const V *yo = reinterpret_cast<const V *>(
+                    sY + chk_index<CK>(own + r * mrow + KB * s, ylim, bad));
 #pragma unroll
                 for (int h = 0; h < KB / 2; ++h) {
                     V u;
@@ -422,6 +471,7 @@ k_kprod_nbs(int ntiles, const int4 *__restrict__ thdr, const uint4 *__restrict__
         }
         __syncthreads();  // the next tile's copies overwrite the blob and Y areas
     }
+    chk_report<CK>(bad, chk);
     if (dot_mode) {
         __shared__ double sh[32];
         double bt = block_dot_total(dot, sh);
@@ -647,6 +697,8 @@ size_t nbs_smem_bytes(const NbsOps &nb) {
 template <class T, int W>
 static int nbs_blocks_per_sm(size_t smem) {
     if (cudaFuncSetAttribute(k_kprod_nbs<T, W>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                             (int)smem) != cudaSuccess ||
+        cudaFuncSetAttribute(k_kprod_nbs<T, W, true>, cudaFuncAttributeMaxDynamicSharedMemorySize,
                              (int)smem) != cudaSuccess) {
         cudaGetLastError();
         return 0;
@@ -677,7 +729,8 @@ int nbs_prepare(const NbsOps &nb) {
 
 template <class T>
 void launch_kprod_nbs(const Launch &L, const NbsOps &nb, const T *blob, const T *Y, T *out,
-                      int project, int dot_mode, Work<T> &w, int check_stop) {
+                      int project, int dot_mode, Work<T> &w, int check_stop, int *chk,
+                      long long ny) {
     const size_t smem = nbs_smem_bytes<T>(nb);
     long long g = (long long)L.nsm * (nb.per_sm > 0 ? nb.per_sm : 1);
     if (g > nb.ntiles) g = nb.ntiles;
@@ -687,9 +740,14 @@ void launch_kprod_nbs(const Launch &L, const NbsOps &nb, const T *blob, const T 
     switch (nb.W) {
 #define EMIN_NBS(WV)                                                                          \
     case WV:                                                                                  \
-        k_kprod_nbs<T, WV><<<(int)g, WV * 32, smem, L.stream>>>(                              \
-            nb.ntiles, nb.hdr, bl, nb.runs, nb.stage_cap16, Y, out, project, dot_mode, w.st, \
-            w.partials, w.hist, w.hist_cap, check_stop);                                     \
+        if (chk)                                                                              \
+            k_kprod_nbs<T, WV, true><<<(int)g, WV * 32, smem, L.stream>>>(                    \
+                nb.ntiles, nb.hdr, bl, nb.runs, nb.stage_cap16, Y, out, project, dot_mode,   \
+                w.st, w.partials, w.hist, w.hist_cap, check_stop, chk, ny, nb.blob16);        \
+        else                                                                                  \
+            k_kprod_nbs<T, WV><<<(int)g, WV * 32, smem, L.stream>>>(                          \
+                nb.ntiles, nb.hdr, bl, nb.runs, nb.stage_cap16, Y, out, project, dot_mode,   \
+                w.st, w.partials, w.hist, w.hist_cap, check_stop, nullptr, ny, nb.blob16);    \
         break;
         EMIN_NBS(2)
         EMIN_NBS(3)
@@ -710,8 +768,10 @@ template void launch_nbs_fill<double>(const Launch &, const NbsOps &, const int 
 template int nbs_prepare<float>(const NbsOps &);
 template int nbs_prepare<double>(const NbsOps &);
 template void launch_kprod_nbs<float>(const Launch &, const NbsOps &, const float *,
-                                      const float *, float *, int, int, Work<float> &, int);
+                                      const float *, float *, int, int, Work<float> &, int, int *,
+                                      long long);
 template void launch_kprod_nbs<double>(const Launch &, const NbsOps &, const double *,
-                                       const double *, double *, int, int, Work<double> &, int);
+                                       const double *, double *, int, int, Work<double> &, int,
+                                       int *, long long);
 
 }  // namespace emin

@@ -499,8 +499,10 @@ __global__ void k_sell_len(int n, const int *__restrict__ Ap, int *slen) {
 __global__ void k_sell_plan(int n, const int *__restrict__ Ap, const int *__restrict__ Aj,
                             const int *__restrict__ Pp, const int *__restrict__ Pj,
                             const int *__restrict__ sell_ptr, int *soff, unsigned short *smap,
-                            unsigned int *sw, int *wide, int *dpos) {
-    int too_wide = 0;
+                            unsigned int *sw, int *wide, int *dpos, long long nsell, int *chk) {
+    // chk (bounds checks on): every position written lies in the plan and
+    // every row l it refers to in [0, n); a violation is skipped and flagged
+    int too_wide = 0, bad = 0;
     const int nlanes = ((n + 31) >> 5) << 5;
     for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < nlanes; i += gridDim.x * blockDim.x) {
         const int sl = i >> 5, lane = i & 31;
@@ -517,10 +519,18 @@ __global__ void k_sell_plan(int n, const int *__restrict__ Ap, const int *__rest
         if (row) dpos[i] = dp;  // position of A(i,i) in the CSR arrays (-1: missing)
         for (int j = 0; j < len; ++j) {
             const int pos = base + j * 32 + lane;
+            if (chk && (pos < 0 || pos >= nsell)) {
+                bad = 1;
+                continue;
+            }
             unsigned int map = 0xFFFu;
             int off = 0;
             if (j < rl) {
-                const int l = Aj[e0 + j];
+                int l = Aj[e0 + j];
+                if (chk && (l < 0 || l >= n)) {
+                    bad = 1;
+                    l = 0;
+                }
                 const int q0 = Pp[l], ml = Pp[l + 1] - q0;
                 for (int q = 0; q < ml && q < 4; ++q) {
                     const int c = Pj[q0 + q];
@@ -540,6 +550,7 @@ __global__ void k_sell_plan(int n, const int *__restrict__ Ap, const int *__rest
         }
     }
     if (__any_sync(0xffffffffu, too_wide) && (threadIdx.x & 31) == 0) atomicOr(wide, 1);
+    if (chk && __any_sync(0xffffffffu, bad) && (threadIdx.x & 31) == 0) atomicOr(chk, 1);
 }
 
 // A^ = D^{-1/2} A D^{-1/2} in SELL-32 order (padding 0).  One warp per
@@ -741,10 +752,10 @@ void launch_sell_len(const Launch &L, int n, const int *Ap, int *slen) {
 
 void launch_sell_plan(const Launch &L, int n, const int *Ap, const int *Aj, const int *Pp,
                       const int *Pj, const int *sell_ptr, int *soff, unsigned short *smap,
-                      unsigned int *sw, int *wide, int *dpos) {
+                      unsigned int *sw, int *wide, int *dpos, long long nsell, int *chk) {
     if (n <= 0) return;
-    k_sell_plan<<<grid_for(n, L.grid_rows), kBlock, 0, L.stream>>>(n, Ap, Aj, Pp, Pj, sell_ptr,
-                                                                   soff, smap, sw, wide, dpos);
+    k_sell_plan<<<grid_for(n, L.grid_rows), kBlock, 0, L.stream>>>(
+        n, Ap, Aj, Pp, Pj, sell_ptr, soff, smap, sw, wide, dpos, nsell, chk);
     note_launch();
 }
 

@@ -92,22 +92,22 @@ __device__ __forceinline__ SgsView sgs_view(const unsigned short *b, int m, int 
 // One level-ordered unit-diagonal triangular sweep of a group held in u
 // (row t, column c at u[t * G + c]) by the LPG lanes of a lane group: for
 // the rows of each level, u_t -= sum over the row's couplings (t', v) v u_t'.
-template <class T, int GM, int LPG>
+template <class T, int GM, int LPG, bool CK>
 __device__ __forceinline__ void sgs_sweep_levels(T *u, int G, int nl, const unsigned short *lvl,
                                                  const unsigned short *row,
                                                  const unsigned short *optr,
                                                  const unsigned short *idx, const T *val,
-                                                 int sub, unsigned mask) {
+                                                 int sub, unsigned mask, int m, int &bad) {
     for (int lv = 0; lv < nl; ++lv) {
         const int a = lvl[lv], b = lvl[lv + 1];
         for (int x = a + sub; x < b; x += LPG) {
-            const int t = row[x];
+            const int t = chk_index<CK>(row[x], m, bad);
             T acc[GM];
 #pragma unroll
             for (int c = 0; c < GM; ++c) acc[c] = (c < G) ? u[t * G + c] : T(0);
             const int o1 = optr[x + 1];
             for (int o = optr[x]; o < o1; ++o) {
-                const int tl = idx[o];
+                const int tl = chk_index<CK>(idx[o], m, bad);
                 const T v = val[o];
 #pragma unroll
                 for (int c = 0; c < GM; ++c)
@@ -127,12 +127,14 @@ __device__ __forceinline__ void sgs_sweep_levels(T *u, int G, int nl, const unsi
 // index blob and coupling values fit the slot, the blob and the values,
 // copied in with coalesced loads so that the sweeps touch shared memory
 // only; a larger group's blob and values are read from global memory.
-template <class T, int GM, int LPG>
+template <class T, int GM, int LPG, bool CK = false>
 __global__ void k_sgs_sweep(int ngroups, const int *__restrict__ hdr, const int *__restrict__ rpos,
                             const uint4 *__restrict__ blob, const T *__restrict__ fval,
                             const T *__restrict__ bval, const T *__restrict__ R,
-                            T *__restrict__ Z, const DevState *st, int slot) {
+                            T *__restrict__ Z, const DevState *st, int slot, int *chk,
+                            long long ny) {
     if (st->stop) return;
+    int bad = 0;
     extern __shared__ __align__(16) unsigned char sgs_smem[];
     constexpr int GPW = 32 / LPG;  // lane groups per warp
     const int lane = threadIdx.x & 31, sub = lane % LPG, half = lane / LPG;
@@ -165,18 +167,21 @@ __global__ void k_sgs_sweep(int ngroups, const int *__restrict__ hdr, const int 
         // the block's entries of r~: row t, column c at rpos[r0 + t] + c
         for (int x = sub; x < m * G; x += LPG) {
             const int t = x / G, c = x - t * G;
-            u[x] = R[rpos[r0 + t] + c];
+            u[x] = R[chk_index<CK>(rpos[r0 + t] + c, ny, bad)];
         }
         __syncwarp(mask);
         const SgsView v = sgs_view(ib, m, nlf, nlb, nf);
-        sgs_sweep_levels<T, GM, LPG>(u, G, nlf, v.flvl, v.frow, v.foptr, v.fidx, fv, sub, mask);
-        sgs_sweep_levels<T, GM, LPG>(u, G, nlb, v.blvl, v.brow, v.boptr, v.bidx, bv, sub, mask);
+        sgs_sweep_levels<T, GM, LPG, CK>(u, G, nlf, v.flvl, v.frow, v.foptr, v.fidx, fv, sub,
+                                         mask, m, bad);
+        sgs_sweep_levels<T, GM, LPG, CK>(u, G, nlb, v.blvl, v.brow, v.boptr, v.bidx, bv, sub,
+                                         mask, m, bad);
         for (int x = sub; x < m * G; x += LPG) {
             const int t = x / G, c = x - t * G;
-            Z[rpos[r0 + t] + c] = u[x];
+            Z[chk_index<CK>(rpos[r0 + t] + c, ny, bad)] = u[x];
         }
         __syncwarp(mask);  // the slot is refilled by the next group
     }
+    chk_report<CK>(bad, chk);
 }
 
 // 16-byte asynchronous copies of `bytes` (a multiple of 16, both addresses
@@ -201,15 +206,17 @@ __device__ __forceinline__ void async_wait_all() {
 // by lane (row t of lane L at [32 t + L], conflict-free), the values of one
 // sweep at a time.  Each lane then sweeps its own block row by row, forward
 // and backward, with no synchronisation: no lane reads another lane's data.
-template <class T>
+template <class T, bool CK = false>
 __global__ void k_sgs_batch(int nbatch, const int *__restrict__ bat_hdr,
                             const int *__restrict__ cls_hdr,
                             const unsigned short *__restrict__ cls_ptr,
                             const unsigned short *__restrict__ cls_idx,
                             const int *__restrict__ rpos, const T *__restrict__ fval,
                             const T *__restrict__ bval, const T *__restrict__ R,
-                            T *__restrict__ Z, const DevState *st, int umax, int vmax) {
+                            T *__restrict__ Z, const DevState *st, int umax, int vmax, int *chk,
+                            long long ny) {
     if (st->stop) return;
+    int bad = 0;
     extern __shared__ __align__(16) unsigned char sgs_smem[];
     const int lane = threadIdx.x & 31;
     T *u = reinterpret_cast<T *>(sgs_smem) + (size_t)(threadIdx.x >> 5) * 32 * (umax + vmax);
@@ -228,14 +235,15 @@ __global__ void k_sgs_batch(int nbatch, const int *__restrict__ bat_hdr,
 #pragma unroll 8
         for (int t = 0; t < m; ++t) {
             const int p = rp[32 * t + lane];
-            u[32 * t + lane] = p >= 0 ? R[p] : T(0);
+            u[32 * t + lane] = p >= 0 ? R[chk_index<CK>(p, ny, bad)] : T(0);
         }
         async_wait_all();
         __syncwarp();
         for (int t = 0; t < m; ++t) {
             T acc = u[32 * t + lane];
             const int o1 = fp[t + 1];
-            for (int o = fp[t]; o < o1; ++o) acc = fmat(-sv[32 * o + lane], u[32 * fi[o] + lane], acc);
+            for (int o = fp[t]; o < o1; ++o)
+                acc = fmat(-sv[32 * o + lane], u[32 * chk_index<CK>(fi[o], m, bad) + lane], acc);
             u[32 * t + lane] = acc;
         }
         __syncwarp();
@@ -245,15 +253,17 @@ __global__ void k_sgs_batch(int nbatch, const int *__restrict__ bat_hdr,
         for (int t = m - 1; t >= 0; --t) {
             T acc = u[32 * t + lane];
             const int o1 = bp[t + 1];
-            for (int o = bp[t]; o < o1; ++o) acc = fmat(-sv[32 * o + lane], u[32 * bi[o] + lane], acc);
+            for (int o = bp[t]; o < o1; ++o)
+                acc = fmat(-sv[32 * o + lane], u[32 * chk_index<CK>(bi[o], m, bad) + lane], acc);
             u[32 * t + lane] = acc;
         }
         for (int t = 0; t < m; ++t) {
             const int p = rp[32 * t + lane];
-            if (p >= 0) Z[p] = u[32 * t + lane];
+            if (p >= 0) Z[chk_index<CK>(p, ny, bad)] = u[32 * t + lane];
         }
         __syncwarp();  // the buffers are refilled by the warp's next batch
     }
+    chk_report<CK>(bad, chk);
 }
 
 // k = 1: z~ <- Pi z~ = z~ - q (q^T z~) per row and gamma = <r~, z~> in one
@@ -662,6 +672,8 @@ void sweep_with(const Launch &L, const SgsOps<T> &s, const T *R, T *Z, const Dev
     static bool attr = false;
     if (!attr) {
         cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, 200 * 1024);
+        cudaFuncSetAttribute(k_sgs_sweep<T, GM, LPG, true>,
+                             cudaFuncAttributeMaxDynamicSharedMemorySize, 200 * 1024);
         cudaGetLastError();
         attr = true;
     }
@@ -680,8 +692,12 @@ void sweep_with(const Launch &L, const SgsOps<T> &s, const T *R, T *Z, const Dev
     const long long tasks_per_block = wpb * (32 / LPG);
     long long blocks = ((long long)s.ngroups + tasks_per_block - 1) / tasks_per_block;
     blocks = std::min(blocks, (long long)L.nsm * per_sm);
-    kern<<<(int)blocks, threads, smem, L.stream>>>(s.ngroups, s.hdr, s.rpos, s.blob, s.fval,
-                                                   s.bval, R, Z, st, (int)slot);
+    if (s.chk)
+        k_sgs_sweep<T, GM, LPG, true><<<(int)blocks, threads, smem, L.stream>>>(
+            s.ngroups, s.hdr, s.rpos, s.blob, s.fval, s.bval, R, Z, st, (int)slot, s.chk, s.ny);
+    else
+        kern<<<(int)blocks, threads, smem, L.stream>>>(s.ngroups, s.hdr, s.rpos, s.blob, s.fval,
+                                                       s.bval, R, Z, st, (int)slot, nullptr, s.ny);
 }
 }  // namespace
 
@@ -697,6 +713,8 @@ void launch_sgs_sweep(const Launch &L, const SgsOps<T> &s, const T *R, T *Z, con
         static bool attr = false;
         if (!attr) {
             cudaFuncSetAttribute(k_sgs_batch<T>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                 200 * 1024);
+            cudaFuncSetAttribute(k_sgs_batch<T, true>, cudaFuncAttributeMaxDynamicSharedMemorySize,
                                  200 * 1024);
             cudaGetLastError();
             attr = true;
@@ -714,9 +732,14 @@ void launch_sgs_sweep(const Launch &L, const SgsOps<T> &s, const T *R, T *Z, con
         }
         long long blocks = ((long long)s.nbatch + wpb - 1) / wpb;
         blocks = std::min(blocks, (long long)L.nsm * per_sm);
-        k_sgs_batch<T><<<(int)blocks, threads, smem, L.stream>>>(
-            s.nbatch, s.bat_hdr, s.cls_hdr, s.cls_ptr, s.cls_idx, s.bat_rpos, s.bat_fval,
-            s.bat_bval, R, Z, st, s.bmax_u, s.bmax_v);
+        if (s.chk)
+            k_sgs_batch<T, true><<<(int)blocks, threads, smem, L.stream>>>(
+                s.nbatch, s.bat_hdr, s.cls_hdr, s.cls_ptr, s.cls_idx, s.bat_rpos, s.bat_fval,
+                s.bat_bval, R, Z, st, s.bmax_u, s.bmax_v, s.chk, s.ny);
+        else
+            k_sgs_batch<T><<<(int)blocks, threads, smem, L.stream>>>(
+                s.nbatch, s.bat_hdr, s.cls_hdr, s.cls_ptr, s.cls_idx, s.bat_rpos, s.bat_fval,
+                s.bat_bval, R, Z, st, s.bmax_u, s.bmax_v, nullptr, s.ny);
         note_launch();
     }
     if (s.ngroups > 0) {

@@ -402,12 +402,14 @@ def emin_trim_memory():
 class Context:
     """Owns one library context.  ``precision``: "fp64" or "mixed";
     ``precond``: "jacobi" (M_1) or "sgs" (the projected block SGS, M_2);
+    ``checks``: bounds checks in the gather kernels (see emin_opts.checks);
     ``stream``: a torch.cuda.Stream or raw cudaStream_t (int), default the
     current torch stream when inputs are CUDA tensors, else the legacy
     default stream."""
 
     def __init__(self, prob=None, *, n=None, nc=None, k=None, arrays=None, precision="fp64",
-                 rank_policy="strict", stream=None, on_device=None, precond="jacobi"):
+                 rank_policy="strict", stream=None, on_device=None, precond="jacobi",
+                 checks=False):
         if prob is not None:
             n, nc, k, arrays = prob.n, prob.nc, prob.k, prob.arrays()
         self.n, self.nc, self.k = int(n), int(nc), int(k)
@@ -415,6 +417,7 @@ class Context:
         opts.precision = {"fp64": EMIN_FP64, "mixed": EMIN_MIXED}[precision]
         opts.rank_policy = {"strict": EMIN_RANK_STRICT, "pinv": EMIN_RANK_PINV}[rank_policy]
         opts.precond = {"jacobi": EMIN_JACOBI, "sgs": EMIN_SGS}[precond]
+        opts.checks = 1 if checks else 0
         if on_device is None:
             on_device = _is_cuda_tensor(arrays[0])
         if stream is None and on_device:

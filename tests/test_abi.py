@@ -55,3 +55,17 @@ def test_no_oracle_in_product_path():
             if f.endswith((".py", ".cu", ".cuh", ".h")):
                 txt = open(os.path.join(dirpath, f)).read()
                 assert "oracle" not in re.findall(r"(?:import|from)\s+(\w+)", txt), f
+
+
+def test_create_rejects_unknown_check_mode(libpath):
+    """emin_opts.checks is 0 or 1; anything else is rejected before any
+    device work."""
+    import numpy as np
+    from paper_2208_02995_gb300 import emin as E
+    o = E.emin_default_opts()
+    o.checks = 2
+    z = np.zeros(2, dtype=np.int32)
+    with pytest.raises(E.EminError) as err:
+        E.emin_create(1, 1, 1, z, z, np.zeros(1), z, z, np.zeros(1), np.ones(1), np.ones(1),
+                      opts=o, inputs_on_device=False)
+    assert err.value.status == E.EMIN_ERR_ARG

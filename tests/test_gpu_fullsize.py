@@ -131,8 +131,11 @@ def test_heterogeneous_elasticity_adjoint_matches_oracle():
     assert relf(P, Pr) <= 1e-9
     _, dLdP, _ = c.energy_grad(P, 1.0, want_energy=False, want_dX=True)
     dLdP = dLdP + 2 * P
-    dA, dB, steps = c.backward(dLdP, 600, 0.0)
-    dA_ref, dB_ref, _, _ = o.backward(Pr, 2 * o.kprod(Pr) + 2 * Pr, 600)
+    # the adjoint runs to dE_k < 1e-24 dE_1 (its solution to about 1e-12),
+    # short of the rounding level where y^T K y of this ill-conditioned
+    # operator can lose its sign
+    dA, dB, steps = c.backward(dLdP, 600, 1e-24)
+    dA_ref, dB_ref, _, _ = o.backward(Pr, 2 * o.kprod(Pr) + 2 * Pr, 600, 1e-24)
     assert steps > 0
     assert relf(dA, dA_ref) <= 1e-8
     assert relf(dB, dB_ref) <= 1e-8
@@ -171,10 +174,20 @@ def test_workload5_full_size_mixed_with_adjoint():
 def test_workload5_adjoint_finite_differences():
     """Workload 5 at full size (2.65M rows, heterogeneous elasticity): the
     implicit-adjoint gradient of L = tr(P^T A P) + ||P||_F^2 after an FP64
-    forward run to the convergence floor, against central differences on 4
-    seeded entries of A (symmetric pairs) and 4 of B (seed 4), the perturbed
-    solves warm-started from P* and run to the floor as well; differences of
-    L formed locally (as for workload 4), relative error <= 1e-6."""
+    forward run to convergence, against central differences along two seeded
+    directions: every stored entry of A scaled by 1 + t s_e (s = +-1,
+    symmetric pairs alike) and B + t dB (dB normal), t = +-1e-4.  Single
+    entries of this operator are too small for their perturbation to rise
+    above the solver's rounding floor; a whole-matrix direction moves P by
+    far more than that floor.  The base solve and the adjoint stop at
+    dE_k < 1e-16 dE_1; the perturbed solves, warm-started from P*, at
+    dE_k < 1e-12 dE_1 of their own (run further, this operator's y^T K y
+    reaches rounding level and loses its sign).  That limits the accuracy
+    of the difference quotient itself (measured: 3.6e-5 relative along the
+    A direction), so the bar here is 1e-4; the gradient's own accuracy is
+    checked to 1e-8 against the oracle's adjoint on the 16^3-node case.
+    Differences of L are formed locally, never as a difference of two
+    global totals."""
     import torch
     from paper_2208_02995_gb300.emin import Context
     prob = I.config(5)
@@ -182,61 +195,48 @@ def test_workload5_adjoint_finite_differences():
     dev = lambda a: torch.from_numpy(np.ascontiguousarray(a)).cuda()
     arrays = [dev(a) for a in prob.arrays()]
     Ad, Bd = arrays[2], arrays[6]
-    its = 1500
+    its, tau, tau_pert, t = 1500, 1e-16, 1e-12, 1e-4
     base = Context(n=n, nc=prob.nc, k=k, arrays=arrays)
-    base.iterate(its)
+    base.iterate(its, tau)
     P = torch.empty(prob.nnz_p, dtype=torch.float64, device="cuda")
     base.get_p(P)
     _, dE, dEA = base.energy_grad(P, 1.0, want_energy=False, want_dX=True, want_dA=True)
-    dA, dB, adj_steps = base.backward(dE + 2 * P, its, 0.0)
-    gA = (dA + dEA).cpu().numpy()
-    gB = dB.cpu().numpy()
+    gA, gB, adj_steps = base.backward(dE + 2 * P, its, tau)
+    gA = gA + dEA
     assert adj_steps > 0
+    # directions: s symmetric over the stored pairs (s_ab = s_ba)
+    rows = np.repeat(np.arange(n), np.diff(prob.A_rowptr))
+    lo = np.minimum(rows, prob.A_col).astype(np.int64)
+    hi = np.maximum(rows, prob.A_col).astype(np.int64)
+    key = (lo * n + hi + 4).astype(np.uint64)  # seed 4 in the key
+    with np.errstate(over="ignore"):
+        bit = (key * np.uint64(0x9E3779B97F4A7C15)) >> np.uint64(63)  # a multiplicative hash
+    s = np.where(bit == 0, 1.0, -1.0)
+    SA = dev(prob.A_val * s)                       # dA/dt
+    dB = dev(np.random.default_rng(4).standard_normal((n, k)))
     pert = Context(n=n, nc=prob.nc, k=k, arrays=arrays)
     Pp, Pm = (torch.empty_like(P) for _ in range(2))
-    prow, Pcol = prob.P_rowptr, prob.P_col
 
-    def solve(A=None, B=None, out=None):
-        pert.set_values(A_val=Ad if A is None else A, B=Bd if B is None else B, P0_val=P,
-                        on_device=True)
-        pert.iterate(its)
+    def solve(A, B, out):
+        pert.set_values(A_val=A, B=B, P0_val=P, on_device=True)
+        pert.iterate(its, tau_pert)
         pert.get_p(out)
 
-    def row_dot(Pv, a, b):
-        ra = slice(int(prow[a]), int(prow[a + 1]))
-        rb = slice(int(prow[b]), int(prow[b + 1]))
-        va = dict(zip(Pcol[ra].tolist(), Pv[ra].cpu().tolist()))
-        return sum(va.get(c, 0.0) * v for c, v in zip(Pcol[rb].tolist(), Pv[rb].cpu().tolist()))
+    def common():
+        d, sm = Pp - Pm, Pp + Pm
+        return float(torch.dot(d, base.kprod(sm, project=False)) + torch.dot(d, sm))
 
-    def dL_common():
-        d, s = Pp - Pm, Pp + Pm
-        return float(torch.dot(d, base.kprod(s, project=False)) + torch.dot(d, s))
-
-    rows = np.repeat(np.arange(n), np.diff(prob.A_rowptr))
-    rng = np.random.default_rng(4)
-    for e in rng.choice(prob.nnz_a, 4, replace=False):
-        a, b = int(rows[e]), int(prob.A_col[e])
-        lo, hi = prob.A_rowptr[b], prob.A_rowptr[b + 1]
-        mirror = lo + int(np.searchsorted(prob.A_col[lo:hi], a))
-        h = 1e-4 * max(abs(prob.A_val[e]), 1.0)
-        for sgn, out in ((1.0, Pp), (-1.0, Pm)):
-            Ah = Ad.clone()
-            Ah[e] += sgn * h
-            if mirror != e:
-                Ah[mirror] += sgn * h
-            solve(A=Ah, out=out)
-        w = 1.0 if a == b else 2.0
-        explicit = h * w * (row_dot(Pp, a, b) + row_dot(Pm, a, b))
-        fd = (dL_common() + explicit) / (2 * h)
-        g = gA[e] + (gA[mirror] if mirror != e else 0.0)
-        assert abs(fd - g) <= 1e-6 * max(abs(g), 1e-8 * np.abs(gA).max()), (e, a, b, fd, g)
-    for idx in rng.choice(n * k, 4, replace=False):
-        i, c = divmod(int(idx), k)
-        h = 1e-4 * max(abs(prob.B[i, c]), 1.0)
-        for sgn, out in ((1.0, Pp), (-1.0, Pm)):
-            Bh = Bd.clone()
-            Bh[i, c] += sgn * h
-            solve(B=Bh, out=out)
-        fd = dL_common() / (2 * h)
-        g = gB[i, c]
-        assert abs(fd - g) <= 1e-6 * max(abs(g), 1e-8 * np.abs(gB).max()), (i, c, fd, g)
+    # direction in A: L(+) - L(-) = <P+ - P-, A (P+ + P-)> + <P+ - P-, P+ + P->
+    #                              + t (<P+, S P+> + <P-, S P->),  S = dA/dt
+    solve(Ad + t * SA, Bd, Pp)
+    solve(Ad - t * SA, Bd, Pm)
+    explicit = t * float(torch.dot(SA, base.outer(Pp, Pp) + base.outer(Pm, Pm)))
+    fd = (common() + explicit) / (2 * t)
+    g = float(torch.dot(gA, SA))
+    assert abs(fd - g) <= 1e-4 * abs(g), (fd, g)
+    # direction in B (L has no explicit dependence on B)
+    solve(Ad, Bd + t * dB, Pp)
+    solve(Ad, Bd - t * dB, Pm)
+    fd = common() / (2 * t)
+    g = float(torch.sum(gB * dB))
+    assert abs(fd - g) <= 1e-4 * abs(g), (fd, g)
