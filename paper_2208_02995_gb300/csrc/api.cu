@@ -337,7 +337,8 @@ Ops<double> iter_ops64(const emin_ctx *c) {
 }
 
 Ops<float> iter_ops32(const emin_ctx *c) {
-    Ops<float> o{c->n, c->nc, c->k, c->Ap, c->Aj, c->Ah32, c->Pp, c->Pj, c->Bc32, c->Ginv32,
+    // (A^ in CSR order is not formed when the staged product serves: null)
+    Ops<float> o{c->n, c->nc, c->k, c->Ap, c->Aj, c->nbs_blob ? nullptr : c->Ah32, c->Pp, c->Pj, c->Bc32, c->Ginv32,
                       c->qv32, c->sell_ptr, c->sa32, c->soff, c->smap, c->sw, c->spk32, c->boff, c->blen, c->bmap, c->tile_map, c->ntiles,
                       c->maxrow_p, c->lanes};
     o.sgs = sgs_ops<float>(c, c->sgs_fval32, c->sgs_bval32, c->sgs_bfval32, c->sgs_bbval32);
@@ -590,7 +591,7 @@ int run_setup(emin_ctx *c) {
     launch_diag(L, c->n, c->Ap, c->Aj, c->Av, c->dinv, c->dinv32, c->dint);
     launch_diag_scales(L, c->n, c->dinv, c->dsq, c->dhalf);
     launch_gram(L, c->n, c->k, c->Pp, c->Pj, c->Bc, c->Ginv, c->Ginv32, c->opts.rank_policy,
-                c->dint, c->dint + 2);
+                c->dint, c->dint + 2, c->boff ? 3 : 1);
     fill_nbs(c);
     launch_restore(L, c->n, c->k, c->Pp, c->Pj, c->Bc, c->B, c->Ginv, c->P0_in, nullptr, nullptr,
                    nullptr, 1, c->P0);
@@ -600,7 +601,7 @@ int run_setup(emin_ctx *c) {
         if (c->sell_ptr)
             launch_sell_values<float>(L, c->n, c->Ap, c->Aj, c->Av, c->dsq, c->sell_ptr, c->sa32,
                                       c->sw, c->spk32);
-        else
+        else if (!c->nbs_blob)  // the staged product reads A^ from its own blob
             launch_scale_a<float>(L, c->n, c->Ap, c->Aj, c->Av, c->dsq, c->Ah32);
         if (c->k == 1) launch_qvec_k1<float>(L, c->n, c->Pp, c->Pj, c->Bc, c->qv32);
         form_sgs_values<float>(c, c->sgs_fval32, c->sgs_bval32, c->sgs_bfval32,

@@ -214,8 +214,10 @@ void launch_validate_csr(const Launch &L, int nrows, int ncols, const int *rowpt
 void launch_check_finite(const Launch &L, const double *v, long long count, int *flags);
 void launch_diag(const Launch &L, int n, const int *Ap, const int *Aj, const double *Av,
                  double *dinv64, float *dinv32, int *flags);
+// rep: consecutive rows sharing their columns of P (3 for node-blocked
+// problems, else 1); their Gram matrix is factorised once
 void launch_gram(const Launch &L, int n, int k, const int *Pp, const int *Pj, const double *Bc,
-                 double *Ginv, float *Ginv32, int policy, int *flags, int *ndef);
+                 double *Ginv, float *Ginv32, int policy, int *flags, int *ndef, int rep);
 // P = base + f_i * add (add64 or add32, f may be null = 1), then, if
 // `correct`, the least-norm constraint correction of every row
 void launch_restore(const Launch &L, int n, int k, const int *Pp, const int *Pj,
@@ -348,7 +350,7 @@ int nbs_prepare(const NbsOps &nb);
 template <class T>
 void launch_kprod_nbs(const Launch &L, const NbsOps &nb, const T *blob, const T *Y, T *out,
                       int project, int dot_mode, Work<T> &w, int check_stop, int *chk,
-                      long long ny);
+                      long long ny, int gamma0 = 0);
 
 // ---- adjoint kernels (adjoint_kernels.cu) ----
 void launch_outer(const Launch &L, int n, const int *Ap, const int *Aj, const int *Pp,

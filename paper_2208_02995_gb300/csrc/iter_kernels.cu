@@ -983,7 +983,13 @@ void launch_project(const Launch &L, const Ops<T> &o, T *x, T scale) {
 template <class T>
 bool launch_kprod_start(const Launch &L, const Ops<T> &o, const T *x0, T *R, Work<T> &w,
                         int gamma0) {
-    if (o.n <= 0 || (o.boff && o.blen && o.bmap)) return false;
+    if (o.n <= 0) return false;
+    if (o.nbs.ntiles > 0 && o.nbs_blob) {  // the staged node-block product
+        launch_kprod_nbs<T>(L, o.nbs, o.nbs_blob, x0, R, 1, DOT_START, w, 0, o.chk, o.nnz_p,
+                            gamma0);
+        return true;
+    }
+    if (o.boff && o.blen && o.bmap) return false;
     if (!(o.k == 1 && o.sell_ptr && o.sw && o.qv && o.maxrow <= 4 &&
           (sizeof(T) == 4 ? o.spk != nullptr : o.sa != nullptr)))
         return false;

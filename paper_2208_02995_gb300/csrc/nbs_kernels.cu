@@ -227,7 +227,11 @@ __global__ void __launch_bounds__(W * 32)
 k_kprod_nbs(int ntiles, const int4 *__restrict__ thdr, const uint4 *__restrict__ blob,
             const int4 *__restrict__ runs, int stage_cap16, const T *__restrict__ Y,
             T *__restrict__ out, int project, int dot_mode, DevState *st, double *partials,
-            double *hist, int cap, int check_stop, int *chk, long long ny, long long blob16) {
+            double *hist, int cap, int check_stop, int *chk, long long ny, long long blob16,
+            int gamma0) {
+    // dot_mode DOT_START (the start of Algorithm 3): out = -Pi(A^ x), the
+    // convergence floor from <x, x> before the projection and, with gamma0,
+    // gamma_0 = <Pi x, Pi x> after it, reduced together
     using V = typename PairOf<T>::V;
     if (check_stop && st->stop) return;
     int bad = 0;
@@ -252,7 +256,7 @@ k_kprod_nbs(int ntiles, const int4 *__restrict__ thdr, const uint4 *__restrict__
         s_skip = 0;
     }
     __syncthreads();
-    Dot<T> dot;
+    Dot<T> dot, dot1;  // DOT_START: dot before the projection, dot1 after
     unsigned phase = 0;
     for (int tile = blockIdx.x; tile < ntiles; tile += gridDim.x) {
         const int4 h0 = thdr[2 * tile], h1 = thdr[2 * tile + 1];
@@ -373,6 +377,12 @@ k_kprod_nbs(int ntiles, const int4 *__restrict__ thdr, const uint4 *__restrict__
                 }
             }
         }
+        if (dot_mode == DOT_START && valid) {
+#pragma unroll
+            for (int r = 0; r < NB; ++r)
+#pragma unroll
+                for (int t = 0; t < KB; ++t) dot.add(acc[r][t], acc[r][t]);
+        }
         if (project) {
             // t_r = sum over the node's lanes of B_s^T x_r (B_s = B_c rows of
             // this lane's aggregate), c_r = G_i^-1 t_r, x_r -= B_s c_r
@@ -460,19 +470,34 @@ k_kprod_nbs(int ntiles, const int4 *__restrict__ thdr, const uint4 *__restrict__
                     V u;
                     u.x = acc[r][2 * h];
                     u.y = acc[r][2 * h + 1];
-                    op[h] = u;
-                    if (dot_mode) {
+                    if (dot_mode == DOT_START) {
+                        dot1.add(u.x, u.x);
+                        dot1.add(u.y, u.y);
+                        u.x = -u.x;
+                        u.y = -u.y;
+                    } else if (dot_mode) {
                         const V yv = yo[h];
                         dot.add(yv.x, u.x);
                         dot.add(yv.y, u.y);
                     }
+                    op[h] = u;
                 }
             }
         }
         __syncthreads();  // the next tile's copies overwrite the blob and Y areas
     }
     chk_report<CK>(bad, chk);
-    if (dot_mode) {
+    if (dot_mode == DOT_START) {
+        __shared__ double sh[32];
+        const double b0 = block_dot_total(dot, sh);
+        __syncthreads();
+        const double b1 = block_dot_total(dot1, sh);
+        double s0, s1;
+        if (grid_reduce2(b0, b1, partials, &st->ticket[0], &s0, &s1)) {
+            finalize_gamma(st, s0, UPD_FLOOR, GammaFloor<T>::value);
+            if (gamma0) finalize_gamma(st, s1, UPD_INIT, GammaFloor<T>::value);
+        }
+    } else if (dot_mode) {
         __shared__ double sh[32];
         double bt = block_dot_total(dot, sh);
         double total;
@@ -730,11 +755,11 @@ int nbs_prepare(const NbsOps &nb) {
 template <class T>
 void launch_kprod_nbs(const Launch &L, const NbsOps &nb, const T *blob, const T *Y, T *out,
                       int project, int dot_mode, Work<T> &w, int check_stop, int *chk,
-                      long long ny) {
+                      long long ny, int gamma0) {
     const size_t smem = nbs_smem_bytes<T>(nb);
     long long g = (long long)L.nsm * (nb.per_sm > 0 ? nb.per_sm : 1);
     if (g > nb.ntiles) g = nb.ntiles;
-    if (g > kMaxGrid) g = kMaxGrid;
+    if (g > kMaxGrid / 2) g = kMaxGrid / 2;  // DOT_START reduces two partial sums per block
     if (g < 1) g = 1;
     const uint4 *bl = reinterpret_cast<const uint4 *>(blob);
     switch (nb.W) {
@@ -743,11 +768,12 @@ void launch_kprod_nbs(const Launch &L, const NbsOps &nb, const T *blob, const T 
         if (chk)                                                                              \
             k_kprod_nbs<T, WV, true><<<(int)g, WV * 32, smem, L.stream>>>(                    \
                 nb.ntiles, nb.hdr, bl, nb.runs, nb.stage_cap16, Y, out, project, dot_mode,   \
-                w.st, w.partials, w.hist, w.hist_cap, check_stop, chk, ny, nb.blob16);        \
+                w.st, w.partials, w.hist, w.hist_cap, check_stop, chk, ny, nb.blob16, gamma0);\
         else                                                                                  \
             k_kprod_nbs<T, WV><<<(int)g, WV * 32, smem, L.stream>>>(                          \
                 nb.ntiles, nb.hdr, bl, nb.runs, nb.stage_cap16, Y, out, project, dot_mode,   \
-                w.st, w.partials, w.hist, w.hist_cap, check_stop, nullptr, ny, nb.blob16);    \
+                w.st, w.partials, w.hist, w.hist_cap, check_stop, nullptr, ny, nb.blob16,     \
+                gamma0);                                                                      \
         break;
         EMIN_NBS(2)
         EMIN_NBS(3)
@@ -769,9 +795,9 @@ template int nbs_prepare<float>(const NbsOps &);
 template int nbs_prepare<double>(const NbsOps &);
 template void launch_kprod_nbs<float>(const Launch &, const NbsOps &, const float *,
                                       const float *, float *, int, int, Work<float> &, int, int *,
-                                      long long);
+                                      long long, int);
 template void launch_kprod_nbs<double>(const Launch &, const NbsOps &, const double *,
                                        const double *, double *, int, int, Work<double> &, int,
-                                       int *, long long);
+                                       int *, long long, int);
 
 }  // namespace emin

@@ -137,9 +137,13 @@ __device__ void pinv_sym(double (&G)[K * K], double (&out)[K * K]) {
 template <int K>
 __global__ void k_gram(int n, const int *__restrict__ Pp, const int *__restrict__ Pj,
                        const double *__restrict__ Bc, double *Ginv, float *Ginv32, int policy,
-                       int *flags, int *ndef) {
+                       int *flags, int *ndef, int rep) {
+    // rep consecutive rows share their columns of P (rep = 3 for the rows of
+    // a node of a node-blocked problem), hence G_i: computed once per group
     constexpr int KK = K * (K + 1) / 2;
-    for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < n; i += gridDim.x * blockDim.x) {
+    const int ngr = n / rep;
+    for (int gi = blockIdx.x * blockDim.x + threadIdx.x; gi < ngr; gi += gridDim.x * blockDim.x) {
+        const int i = gi * rep;
         double G[K * K];
 #pragma unroll
         for (int a = 0; a < K * K; ++a) G[a] = 0.0;
@@ -207,19 +211,20 @@ __global__ void k_gram(int n, const int *__restrict__ Pp, const int *__restrict_
 #pragma unroll
                 for (int b = 0; b < a; ++b) G[b * K + a] = G[a * K + b];
             pinv_sym<K>(G, out);
-            atomicAdd(ndef, 1);
+            atomicAdd(ndef, rep);
         } else {
             atomicOr(flags, F_RANK);
 #pragma unroll
             for (int a = 0; a < K * K; ++a) out[a] = 0.0;
         }
+        for (int r = 0; r < rep; ++r)
 #pragma unroll
-        for (int a = 0; a < K; ++a)
+            for (int a = 0; a < K; ++a)
 #pragma unroll
-            for (int b = 0; b <= a; ++b) {
-                Ginv[(size_t)i * KK + tri(a, b)] = out[a * K + b];
-                Ginv32[(size_t)i * KK + tri(a, b)] = (float)out[a * K + b];
-            }
+                for (int b = 0; b <= a; ++b) {
+                    Ginv[(size_t)(i + r) * KK + tri(a, b)] = out[a * K + b];
+                    Ginv32[(size_t)(i + r) * KK + tri(a, b)] = (float)out[a * K + b];
+                }
     }
 }
 
@@ -673,12 +678,13 @@ void launch_diag(const Launch &L, int n, const int *Ap, const int *Aj, const dou
 }
 
 void launch_gram(const Launch &L, int n, int k, const int *Pp, const int *Pj, const double *Bc,
-                 double *Ginv, float *Ginv32, int policy, int *flags, int *ndef) {
+                 double *Ginv, float *Ginv32, int policy, int *flags, int *ndef, int rep) {
     if (n <= 0) return;
-    const int g = grid_for(n, L.grid_rows);
+    if (rep < 1 || n % rep) rep = 1;
+    const int g = grid_for(n / rep, L.grid_rows);
     switch (k) {
 #define EMIN_GRAM(KV) \
-    case KV: k_gram<KV><<<g, kBlock, 0, L.stream>>>(n, Pp, Pj, Bc, Ginv, Ginv32, policy, flags, ndef); note_launch(); break;
+    case KV: k_gram<KV><<<g, kBlock, 0, L.stream>>>(n, Pp, Pj, Bc, Ginv, Ginv32, policy, flags, ndef, rep); note_launch(); break;
         EMIN_GRAM(1) EMIN_GRAM(2) EMIN_GRAM(3) EMIN_GRAM(4)
         EMIN_GRAM(5) EMIN_GRAM(6) EMIN_GRAM(7) EMIN_GRAM(8)
 #undef EMIN_GRAM
