@@ -67,14 +67,14 @@ struct emin_ctx {
     int *sgs_hdr = nullptr, *sgs_rpos = nullptr;
     int *sgs_fown = nullptr, *sgs_fa = nullptr, *sgs_bown = nullptr, *sgs_ba = nullptr;
     unsigned short *sgs_blob = nullptr;
-    int sgs_nbatch = 0, sgs_bmax_u = 0, sgs_bmax_v = 0;
-    long long sgs_bnf = 0, sgs_bnb = 0;
+    int sgs_nbatch = 0, sgs_nbucket = 0;
+    SgsBucket sgs_bucket[kSgsBuckets];
+    long long sgs_nbval = 0, sgs_nbrpos = 0, sgs_ncls_blob = 0;
     int *sgs_cls_hdr = nullptr, *sgs_bat_hdr = nullptr, *sgs_bat_rpos = nullptr;
-    int *sgs_bat_fown = nullptr, *sgs_bat_fa = nullptr, *sgs_bat_bown = nullptr,
-        *sgs_bat_ba = nullptr;
-    unsigned short *sgs_cls_ptr = nullptr, *sgs_cls_idx = nullptr;
-    float *sgs_bfval32 = nullptr, *sgs_bbval32 = nullptr;
-    double *sgs_bfval64 = nullptr, *sgs_bbval64 = nullptr;
+    int *sgs_bat_own = nullptr, *sgs_bat_ent = nullptr;
+    unsigned *sgs_cls_blob = nullptr;
+    float *sgs_batval32 = nullptr;
+    double *sgs_batval64 = nullptr;
     float *sgs_fval32 = nullptr, *sgs_bval32 = nullptr;
     double *sgs_fval64 = nullptr, *sgs_bval64 = nullptr;
     double *Pstar = nullptr, *t64c = nullptr;
@@ -293,22 +293,24 @@ Ops<double> plain_ops64(const emin_ctx *c) {
     return o;
 }
 
-// the SGS plan with the values of one precision (an empty plan: Jacobi)
+// the SGS plan with the values of one precision (an empty plan: Jacobi);
+// qv (k = 1) lets a fully batched plan take the fused path
 template <class T>
-SgsOps<T> sgs_ops(const emin_ctx *c, const T *fval, const T *bval, const T *bfval,
-                  const T *bbval) {
+SgsOps<T> sgs_ops(const emin_ctx *c, const T *fval, const T *bval, const T *batval,
+                  const T *qv) {
     SgsOps<T> s;
     if (c->opts.precond != EMIN_SGS || (c->sgs_ngroups <= 0 && c->sgs_nbatch <= 0)) return s;
     s.nbatch = c->sgs_nbatch;
-    s.bmax_u = c->sgs_bmax_u;
-    s.bmax_v = c->sgs_bmax_v;
+    s.nbucket = c->sgs_nbucket;
+    for (int b = 0; b < kSgsBuckets; ++b) s.bucket[b] = c->sgs_bucket[b];
     s.cls_hdr = c->sgs_cls_hdr;
     s.bat_hdr = c->sgs_bat_hdr;
     s.bat_rpos = c->sgs_bat_rpos;
-    s.cls_ptr = c->sgs_cls_ptr;
-    s.cls_idx = c->sgs_cls_idx;
-    s.bat_fval = bfval;
-    s.bat_bval = bbval;
+    s.cls_blob = c->sgs_cls_blob;
+    s.bat_val = batval;
+    s.nbat_rpos = c->sgs_nbrpos;
+    s.nbat_val = c->sgs_nbval;
+    s.ncls_blob = c->sgs_ncls_blob;
     s.ngroups = c->sgs_ngroups;
     s.cap = c->sgs_cap;
     s.gmax = c->sgs_gmax;
@@ -319,6 +321,7 @@ SgsOps<T> sgs_ops(const emin_ctx *c, const T *fval, const T *bval, const T *bfva
     s.blob = reinterpret_cast<const uint4 *>(c->sgs_blob);
     s.fval = fval;
     s.bval = bval;
+    s.fused = c->k == 1 && qv != nullptr && c->sgs_ngroups == 0 && c->sgs_nbatch > 0;
     return s;
 }
 
@@ -327,7 +330,7 @@ Ops<double> iter_ops64(const emin_ctx *c) {
     Ops<double> o{c->n, c->nc, c->k, c->Ap, c->Aj, c->Ah64, c->Pp, c->Pj, c->Bc, c->Ginv,
                        c->qv64, c->sell_ptr, c->sa64, c->soff, c->smap, c->sw, nullptr, c->boff, c->blen, c->bmap, c->tile_map, c->ntiles,
                        c->maxrow_p, c->lanes};
-    o.sgs = sgs_ops<double>(c, c->sgs_fval64, c->sgs_bval64, c->sgs_bfval64, c->sgs_bbval64);
+    o.sgs = sgs_ops<double>(c, c->sgs_fval64, c->sgs_bval64, c->sgs_batval64, c->qv64);
     if (c->nbs_blob && c->opts.precision == EMIN_FP64) {
         o.nbs = c->nbs;
         o.nbs_blob = reinterpret_cast<const double *>(c->nbs_blob);
@@ -341,7 +344,7 @@ Ops<float> iter_ops32(const emin_ctx *c) {
     Ops<float> o{c->n, c->nc, c->k, c->Ap, c->Aj, c->nbs_blob ? nullptr : c->Ah32, c->Pp, c->Pj, c->Bc32, c->Ginv32,
                       c->qv32, c->sell_ptr, c->sa32, c->soff, c->smap, c->sw, c->spk32, c->boff, c->blen, c->bmap, c->tile_map, c->ntiles,
                       c->maxrow_p, c->lanes};
-    o.sgs = sgs_ops<float>(c, c->sgs_fval32, c->sgs_bval32, c->sgs_bfval32, c->sgs_bbval32);
+    o.sgs = sgs_ops<float>(c, c->sgs_fval32, c->sgs_bval32, c->sgs_batval32, c->qv32);
     if (c->nbs_blob && c->opts.precision == EMIN_MIXED) {
         o.nbs = c->nbs;
         o.nbs_blob = reinterpret_cast<const float *>(c->nbs_blob);
@@ -433,7 +436,7 @@ int start_pcg(emin_ctx *c, const Ops<T> &o, Work<T> &w, const T *x0) {
     // on the packed k = 1 plan one launch forms r~, the floor and (Jacobi)
     // gamma_0; otherwise the product, the floor, the projection and gamma_0
     // are separate passes
-    const bool sgs = o.sgs.ngroups > 0;
+    const bool sgs = o.sgs.active();
     const bool fused = x0 && launch_kprod_start<T>(c->L, o, x0, w.R, w, sgs ? 0 : 1);
     if (!fused) {
         if (x0) launch_kprod<T>(c->L, o, x0, w.R, 0, DOT_NONE, w, 0);
@@ -441,9 +444,10 @@ int start_pcg(emin_ctx *c, const Ops<T> &o, Work<T> &w, const T *x0) {
         launch_project<T>(c->L, o, w.R, x0 ? T(-1) : T(1));
     }
     if (sgs) {
-        // z~_0 = Pi (L^ + I)^{-T} (L^ + I)^{-1} r~_0, gamma_0 = <r~, z~>
-        launch_sgs_sweep<T>(c->L, o.sgs, w.R, w.Z, w.st);
-        launch_sgs_finish<T>(c->L, o, w, 1, c->nnz_p);
+        // z~_0 = Pi (L^ + I)^{-T} (L^ + I)^{-1} r~_0, gamma_0 = <r~, z~> (fused:
+        // gamma_0 from the sweep, Pi in the first direction update)
+        launch_sgs_sweep<T>(c->L, o.sgs, w.R, w.Z, w.st, w.partials, 1);
+        if (!o.sgs.fused) launch_sgs_finish<T>(c->L, o, w, 1, c->nnz_p);
     } else if (!fused) {
         launch_update<T>(c->L, c->nnz_p, w, UPD_INIT);
     }
@@ -504,31 +508,32 @@ int build_sgs(emin_ctx *c) {
     EMIN_TRY(upload(c, &c->sgs_fa, h.fa));
     EMIN_TRY(upload(c, &c->sgs_bown, h.bown));
     EMIN_TRY(upload(c, &c->sgs_ba, h.ba));
+    if (const int ps = sgs_prepare(c->L.nsm, h)) {
+        std::snprintf(g_last_error, sizeof(g_last_error),
+                      "SGS plan: the batched sweep's shared memory could not be set up");
+        return ps;
+    }
     c->sgs_nbatch = h.nbatch;
-    c->sgs_bmax_u = h.bmax_u;
-    c->sgs_bmax_v = h.bmax_v;
+    c->sgs_nbucket = h.nbucket;
+    for (int b = 0; b < kSgsBuckets; ++b) c->sgs_bucket[b] = h.bucket[b];
     EMIN_TRY(upload(c, &c->sgs_cls_hdr, h.cls_hdr));
     EMIN_TRY(upload(c, &c->sgs_bat_hdr, h.bat_hdr));
     EMIN_TRY(upload(c, &c->sgs_bat_rpos, h.bat_rpos));
-    EMIN_TRY(upload(c, &c->sgs_bat_fown, h.bat_fown));
-    EMIN_TRY(upload(c, &c->sgs_bat_fa, h.bat_fa));
-    EMIN_TRY(upload(c, &c->sgs_bat_bown, h.bat_bown));
-    EMIN_TRY(upload(c, &c->sgs_bat_ba, h.bat_ba));
-    EMIN_TRY(upload(c, &c->sgs_cls_ptr, h.cls_ptr));
-    EMIN_TRY(upload(c, &c->sgs_cls_idx, h.cls_idx));
-    c->sgs_bnf = (long long)h.bat_fa.size();
-    c->sgs_bnb = (long long)h.bat_ba.size();
+    EMIN_TRY(upload(c, &c->sgs_bat_own, h.bat_own));
+    EMIN_TRY(upload(c, &c->sgs_bat_ent, h.bat_ent));
+    EMIN_TRY(upload(c, &c->sgs_cls_blob, h.cls_blob));
+    c->sgs_nbval = (long long)h.bat_ent.size();
+    c->sgs_nbrpos = (long long)h.bat_rpos.size();
+    c->sgs_ncls_blob = (long long)h.cls_blob.size();
     const long long nf = (long long)h.fa.size(), nb = (long long)h.ba.size();
     if (c->opts.precision == EMIN_MIXED) {
         EMIN_TRY(dalloc(c, &c->sgs_fval32, nf));
         EMIN_TRY(dalloc(c, &c->sgs_bval32, nb));
-        EMIN_TRY(dalloc(c, &c->sgs_bfval32, c->sgs_bnf));
-        EMIN_TRY(dalloc(c, &c->sgs_bbval32, c->sgs_bnb));
+        EMIN_TRY(dalloc(c, &c->sgs_batval32, c->sgs_nbval));
     } else {
         EMIN_TRY(dalloc(c, &c->sgs_fval64, nf));
         EMIN_TRY(dalloc(c, &c->sgs_bval64, nb));
-        EMIN_TRY(dalloc(c, &c->sgs_bfval64, c->sgs_bnf));
-        EMIN_TRY(dalloc(c, &c->sgs_bbval64, c->sgs_bnb));
+        EMIN_TRY(dalloc(c, &c->sgs_batval64, c->sgs_nbval));
     }
     c->sgs_nf = nf;
     c->sgs_nb = nb;
@@ -538,12 +543,12 @@ int build_sgs(emin_ctx *c) {
 // the SGS values A^ at the plan's couplings (level and batched paths), in
 // the precision of T
 template <class T>
-void form_sgs_values(emin_ctx *c, T *fval, T *bval, T *bfval, T *bbval) {
+void form_sgs_values(emin_ctx *c, T *fval, T *bval, T *batval) {
     if (c->opts.precond != EMIN_SGS) return;
     launch_sgs_values<T>(c->L, c->sgs_fown, c->sgs_fa, c->sgs_nf, c->sgs_bown, c->sgs_ba,
                          c->sgs_nb, c->Aj, c->Av, c->dsq, fval, bval);
-    launch_sgs_values<T>(c->L, c->sgs_bat_fown, c->sgs_bat_fa, c->sgs_bnf, c->sgs_bat_bown,
-                         c->sgs_bat_ba, c->sgs_bnb, c->Aj, c->Av, c->dsq, bfval, bbval);
+    launch_sgs_values<T>(c->L, c->sgs_bat_own, c->sgs_bat_ent, c->sgs_nbval, nullptr, nullptr, 0,
+                         c->Aj, c->Av, c->dsq, batval, nullptr);
 }
 
 // A^ and q in double (the FP64 path, or the adjoint of a mixed context)
@@ -553,8 +558,7 @@ void form_scaled64(emin_ctx *c) {
     else
         launch_scale_a<double>(c->L, c->n, c->Ap, c->Aj, c->Av, c->dsq, c->Ah64);
     if (c->k == 1) launch_qvec_k1<double>(c->L, c->n, c->Pp, c->Pj, c->Bc, c->qv64);
-    if (c->sgs_fval64) form_sgs_values<double>(c, c->sgs_fval64, c->sgs_bval64, c->sgs_bfval64,
-                                    c->sgs_bbval64);
+    if (c->sgs_fval64) form_sgs_values<double>(c, c->sgs_fval64, c->sgs_bval64, c->sgs_batval64);
     c->have64 = true;
 }
 
@@ -572,16 +576,14 @@ int run_setup(emin_ctx *c) {
             launch_to_float(L, c->Bc, c->Bc32, (long long)c->nc * c->k);
             launch_sell_values<float>(L, c->n, c->Ap, c->Aj, c->Av, c->dsq, c->sell_ptr, c->sa32,
                                       c->sw, c->spk32, c->dsq32);
-            form_sgs_values<float>(c, c->sgs_fval32, c->sgs_bval32, c->sgs_bfval32,
-                                   c->sgs_bbval32);
+            form_sgs_values<float>(c, c->sgs_fval32, c->sgs_bval32, c->sgs_batval32);
             EMIN_TRY(start_pcg<float>(c, iter_ops32(c), c->w32, c->t32a));
         } else {
             launch_setup_k1<double>(L, c->n, c->dpos, c->Av, c->Pp, c->Pj, c->Bc, c->B, c->P0_in,
                                     c->opts.rank_policy, c->dint, c->dint + 2, c->dsq, c->dhalf,
                                     nullptr, c->Ginv, c->qv64, c->P0, c->t64c);
             launch_sell_values<double>(L, c->n, c->Ap, c->Aj, c->Av, c->dsq, c->sell_ptr, c->sa64);
-            form_sgs_values<double>(c, c->sgs_fval64, c->sgs_bval64, c->sgs_bfval64,
-                                    c->sgs_bbval64);
+            form_sgs_values<double>(c, c->sgs_fval64, c->sgs_bval64, c->sgs_batval64);
             c->have64 = true;
             EMIN_TRY(start_pcg<double>(c, iter_ops64(c), c->w64, c->t64c));
         }
@@ -604,8 +606,7 @@ int run_setup(emin_ctx *c) {
         else if (!c->nbs_blob)  // the staged product reads A^ from its own blob
             launch_scale_a<float>(L, c->n, c->Ap, c->Aj, c->Av, c->dsq, c->Ah32);
         if (c->k == 1) launch_qvec_k1<float>(L, c->n, c->Pp, c->Pj, c->Bc, c->qv32);
-        form_sgs_values<float>(c, c->sgs_fval32, c->sgs_bval32, c->sgs_bfval32,
-                                   c->sgs_bbval32);
+        form_sgs_values<float>(c, c->sgs_fval32, c->sgs_bval32, c->sgs_batval32);
         launch_row_scale<double, float>(L, c->n, c->Pp, c->lanes, c->dhalf, 1.0, c->P0, c->t32a);
         EMIN_TRY(start_pcg<float>(c, iter_ops32(c), c->w32, c->t32a));
     } else {
@@ -917,18 +918,22 @@ int create_impl(emin_ctx *c, const int *A_rowptr, const int *A_col, const double
 template <class T>
 int launch_iterations(emin_ctx *c, const Ops<T> &o, Work<T> &w, int n_iters, bool timed) {
     for (int it = 0; it < n_iters; ++it) {
-        launch_ydir<T>(c->L, c->nnz_p, w);
+        if (o.sgs.fused)
+            launch_ydir_proj_k1<T>(c->L, o.n, o.maxrow, o.Pp, o.qv, w.Z, w.Y, w.st);
+        else
+            launch_ydir<T>(c->L, c->nnz_p, w);
         // external records, so that the events also time the launches when
         // the loop is captured into a graph; every c->timing-th iteration
         const bool t = timed && (it % c->timing) == 0;
         if (t) cudaEventRecordWithFlags(c->events[(size_t)it * 2], c->stream, cudaEventRecordExternal);
         launch_kprod<T>(c->L, o, w.Y, w.Yb, 1, DOT_ALPHA, w, 1);
         if (t) cudaEventRecordWithFlags(c->events[(size_t)it * 2 + 1], c->stream, cudaEventRecordExternal);
-        if (o.sgs.ngroups > 0) {
+        if (o.sgs.active()) {
             // projected SGS: the step, then z~ = Pi M^-1 r~ and gamma = <r~, z~>
+            // (fused: gamma from the sweep, Pi in the next direction update)
             launch_update<T>(c->L, c->nnz_p, w, UPD_XR);
-            launch_sgs_sweep<T>(c->L, o.sgs, w.R, w.Z, w.st);
-            launch_sgs_finish<T>(c->L, o, w, 0, c->nnz_p);
+            launch_sgs_sweep<T>(c->L, o.sgs, w.R, w.Z, w.st, w.partials, 0);
+            if (!o.sgs.fused) launch_sgs_finish<T>(c->L, o, w, 0, c->nnz_p);
         } else {
             launch_update<T>(c->L, c->nnz_p, w, UPD_STEP);
         }
@@ -1514,8 +1519,7 @@ static int call_backward(emin_ctx *c, const double *dL_dP, double *dL_dAval, dou
         if (c->opts.precond == EMIN_SGS && !c->sgs_fval64) {
             EMIN_TRY(dalloc(c, &c->sgs_fval64, c->sgs_nf));
             EMIN_TRY(dalloc(c, &c->sgs_bval64, c->sgs_nb));
-            EMIN_TRY(dalloc(c, &c->sgs_bfval64, c->sgs_bnf));
-            EMIN_TRY(dalloc(c, &c->sgs_bbval64, c->sgs_bnb));
+            EMIN_TRY(dalloc(c, &c->sgs_batval64, c->sgs_nbval));
             c->have64 = false;
         }
     }

@@ -91,22 +91,39 @@ struct Work {
     int gwhile_per_pass = 0;  // kernels in one pass of the while body
 };
 
-// The projected block SGS plan on the device (see sgs.cu): per group a
-// header of 12 ints (rows m, columns G, first plan row r0, index blob offset
-// and length in 16-byte units, first forward / backward coupling, coupling
-// counts, level counts, first column), per plan row the position of its
-// first entry, the uint16 index blobs, and the coupling values A^ of both
-// sweeps in group order.
+// The projected block SGS plan on the device (see sgs.cu).
+// Level path: per group a header of 12 ints (rows m, columns G, first plan
+// row r0, index blob offset and length in 16-byte units, first forward /
+// backward coupling, coupling counts, level counts, first column), per plan
+// row the position of its first entry, the uint16 index blobs, and the
+// coupling values A^ of both sweeps in group order.
+// Batched path: classes of structurally identical one-column groups, 32
+// groups (lanes) per batch, one CTA per batch; per class a header of 8 ints
+// (rows m, couplings nv, forward / backward level counts, word offset of
+// its sweep structure, forward / backward row counts, its padded length in
+// words), per batch 4 ints (class, first position, first value, 0), the
+// positions on P's pattern and the coupling values interleaved by lane.
+// Batches are launched in up to two buckets of similar shared-memory size.
+struct SgsBucket {
+    int b0 = 0, b1 = 0;          // batch range
+    int umax = 0, vmax = 0;      // largest m and nv of the bucket's classes
+    int wmax = 0;                // largest sweep structure (words) of its classes
+    int grid32 = 0, grid64 = 0;  // CTAs (float / double launch)
+};
+constexpr int kSgsBuckets = 2;
+constexpr int kSgsWarps = 8;  // warps of a batched-sweep CTA
+
 template <class T>
 struct SgsOps {
-    // batched path (see sgs.cu): class headers (8 ints: rows m, couplings
-    // nf / nb, forward pointer / index offsets, backward pointer / index
-    // offsets), batch headers (4 ints: class, lane-array offsets of the
-    // positions and of both sweeps' values), lane arrays interleaved by 32
-    int nbatch = 0, bmax_u = 0, bmax_v = 0;
+    int nbatch = 0, nbucket = 0;
+    SgsBucket bucket[kSgsBuckets];
     const int *cls_hdr = nullptr, *bat_hdr = nullptr, *bat_rpos = nullptr;
-    const unsigned short *cls_ptr = nullptr, *cls_idx = nullptr;
-    const T *bat_fval = nullptr, *bat_bval = nullptr;
+    const unsigned *cls_blob = nullptr;
+    const T *bat_val = nullptr;
+    long long nbat_rpos = 0, nbat_val = 0, ncls_blob = 0;
+    // gamma formed by the batched sweep and the projection applied in the
+    // direction update (k = 1, every group batched)
+    bool fused = false;
     int ngroups = 0;
     int cap = 0;                 // largest m * G
     int gmax = 0;                // largest G
@@ -116,6 +133,7 @@ struct SgsOps {
     const T *fval = nullptr, *bval = nullptr;
     int *chk = nullptr;  // bounds checks: the context's check word (null: off)
     long long ny = 0;    // entries of the vectors on P's pattern
+    bool active() const { return nbatch > 0 || ngroups > 0; }
 };
 
 // The staged node-block product (nbs_kernels.cu): tiles of whole nodes, per
@@ -300,9 +318,10 @@ struct SgsHost {
     std::vector<int> hdr, rpos, fown, fa, bown, ba;
     std::vector<unsigned short> blob;
     // batched path: classes of identical structure, batches of 32 groups
-    int nbatch = 0, bmax_u = 0, bmax_v = 0;
-    std::vector<int> cls_hdr, bat_hdr, bat_rpos, bat_fown, bat_fa, bat_bown, bat_ba;
-    std::vector<unsigned short> cls_ptr, cls_idx;
+    int nbatch = 0, nbucket = 0;
+    SgsBucket bucket[kSgsBuckets];
+    std::vector<int> cls_hdr, bat_hdr, bat_rpos, bat_own, bat_ent;
+    std::vector<unsigned> cls_blob;
 };
 int build_sgs_plan(int n, int nc, const int *Ap, const int *Aj, const int *Pp, const int *Pj,
                    SgsHost &out);
@@ -313,8 +332,17 @@ void launch_sgs_values(const Launch &L, const int *fown, const int *fa, long lon
 // z~ <- Pi z~ and gamma = <r~, z~> after the sweep (init: gamma_0)
 template <class T>
 void launch_sgs_finish(const Launch &L, const Ops<T> &o, Work<T> &w, int init, long long nnz_p);
+// z~ = (L^ + I)^{-T} (L^ + I)^{-1} r~ over every group; with s.fused the
+// batched sweep also forms gamma = |(L^ + I)^{-1} r~|^2 (init: gamma_0)
 template <class T>
-void launch_sgs_sweep(const Launch &L, const SgsOps<T> &s, const T *R, T *Z, const DevState *st);
+void launch_sgs_sweep(const Launch &L, const SgsOps<T> &s, const T *R, T *Z, DevState *st,
+                      double *partials, int init);
+// CTAs per bucket of the batched sweep (once per plan, outside any capture)
+int sgs_prepare(int nsm, SgsHost &h);
+// y~ = Pi z~ + beta y~ (k = 1), the direction step of the fused SGS path
+template <class T>
+void launch_ydir_proj_k1(const Launch &L, int n, int maxrow, const int *Pp, const T *qv,
+                         const T *Z, T *Y, const DevState *st);
 void set_adjoint_attributes();
 void launch_state_begin(const Launch &L, DevState *st, double tau, int n_iters);
 // the while-loop control of the captured iteration graph (one thread)

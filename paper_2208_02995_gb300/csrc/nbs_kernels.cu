@@ -26,6 +26,7 @@
 #include <deque>
 #include <vector>
 
+#include "bulk_copy.cuh"
 #include "device_util.cuh"
 #include "emin_internal.cuh"
 
@@ -43,60 +44,6 @@ constexpr int kGStride = NB * kGRow;    // per node
 constexpr int kBStride = KB * KB + 2;   // staged B_c table per aggregate
 
 __device__ __forceinline__ int tri(int a, int b) { return a * (a + 1) / 2 + b; }
-
-__device__ __forceinline__ unsigned smem_addr(const void *p) {
-    return (unsigned)__cvta_generic_to_shared(p);
-}
-
-__device__ __forceinline__ void mbar_init(unsigned long long *bar, unsigned count) {
-    asm volatile("mbarrier.init.shared::cta.b64 [%0], %1;\n" ::"r"(smem_addr(bar)), "r"(count)
-                 : "memory");
-}
-
-__device__ __forceinline__ void mbar_expect_tx(unsigned long long *bar, unsigned bytes) {
-    asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;\n" ::"r"(smem_addr(bar)),
-                 "r"(bytes)
-                 : "memory");
-}
-
-// true once the phase with the given parity has completed
-__device__ __forceinline__ bool mbar_try_wait(unsigned long long *bar, unsigned parity) {
-    unsigned ok;
-    asm volatile(
-        "{\n .reg .pred p;\n"
-        " mbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2;\n"
-        " selp.u32 %0, 1, 0, p;\n}\n"
-        : "=r"(ok)
-        : "r"(smem_addr(bar)), "r"(parity)
-        : "memory");
-    return ok != 0;
-}
-
-__device__ __forceinline__ bool mbar_wait_bounded(unsigned long long *bar, unsigned parity) {
-    for (int it = 0; it < kNbsWaitLimit; ++it)
-        if (mbar_try_wait(bar, parity)) return true;
-    return false;
-}
-
-// global -> shared bulk copy (16-byte aligned addresses, size a multiple of
-// 16), completion counted on the mbarrier
-__device__ __forceinline__ void bulk_g2s(void *dst, const void *src, unsigned bytes,
-                                         unsigned long long *bar) {
-    asm volatile(
-        "cp.async.bulk.shared::cluster.global.mbarrier::complete_tx::bytes [%0], [%1], %2, [%3];\n" ::"r"(
-            smem_addr(dst)),
-        "l"(src), "r"(bytes), "r"(smem_addr(bar))
-        : "memory");
-}
-
-// the initialised mbarrier visible to the asynchronous (TMA) proxy
-__device__ __forceinline__ void fence_mbar_init() {
-    asm volatile("fence.mbarrier_init.release.cluster;\n" ::: "memory");
-}
-
-__device__ __forceinline__ void fence_proxy_async() {
-    asm volatile("fence.proxy.async.shared::cta;\n" ::: "memory");
-}
 
 // Per-tile blob regions, in 16-byte units from the tile's start:
 //   lanes   W*32 ints: node-in-tile | slot << 10 | aggregate-in-tile << 13, -1 padding
@@ -304,10 +251,10 @@ k_kprod_nbs(int ntiles, const int4 *__restrict__ thdr, const uint4 *__restrict__
             }
         }
         if (tid == 0) {
-            if (!mbar_wait_bounded(&bar, phase)) {
+            if (!mbar_wait_bounded(&bar, phase, kNbsWaitLimit)) {
                 st->status = EMIN_ERR_TIMEOUT;
                 st->stop = 2;
-                mbar_wait_bounded(&bar, phase);  // the copies in flight, bounded again
+                mbar_wait_bounded(&bar, phase, kNbsWaitLimit);  // the copies in flight, bounded again
                 s_abort = 1;
             }
         }

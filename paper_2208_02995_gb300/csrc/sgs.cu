@@ -11,11 +11,19 @@
 //
 // Plan (built once per context on the host): columns with identical row
 // sets (the k columns of one aggregate in a node-blocked problem) form one
-// group and share one block; for every row of a group the coupled rows of
-// the same group below it (forward sweep) and above it (backward sweep),
-// with their A entries; the rows of a group ordered by dependency level for
-// each sweep, so that a level's rows are independent.  One warp sweeps one
-// group in shared memory, level by level.
+// group and share one block.  One-column groups of identical structure (the
+// interior aggregates of a structured grid) form classes and are swept in
+// batches of 32, one lane per group, by a CTA whose warps share the rows of
+// each dependency level (the batched path); the other groups are swept one
+// per warp, level by level (the level path).
+//
+// The batched path stores one value per coupling of L^, in forward order;
+// the backward sweep reads the same values transposed, which is the L^T of
+// (L^ + I)^{-T}.  It also forms gamma = r~^T M^{-1} r~ = |(L^ + I)^{-1} r~|^2
+// after the forward sweep: r~ is kept in the range of Pi (every update of
+// it is projected), so <r~, Pi M^{-1} r~> = <r~, M^{-1} r~>, and the
+// projection of z~ is applied in the next direction update instead of a
+// pass of its own.
 #include <cuda_runtime.h>
 
 #include <algorithm>
@@ -23,6 +31,7 @@
 #include <unordered_map>
 #include <vector>
 
+#include "bulk_copy.cuh"
 #include "device_util.cuh"
 #include "convert.cuh"
 #include "emin_internal.cuh"
@@ -32,9 +41,13 @@ namespace {
 
 constexpr int kSgsMaxCols = 8;        // columns per group
 constexpr int kSgsMaxRows = 65535;    // rows per group (16-bit local indices)
-constexpr int kBatchRows = 96;        // rows of a group swept by one lane (batched path)
+constexpr int kBatchRows = 1024;      // rows of a batched group (10-bit local rows)
+constexpr int kBatchRowCpl = 63;      // couplings of one row in one sweep (6-bit counts)
 constexpr int kBatchMin = 8;          // groups of one structure before it is batched
-constexpr int kBatchCouplings = 256;  // couplings per sweep of a batched group
+constexpr int kBatchTail = 1024;      // rarer structures batched too while this few groups have them
+constexpr long long kBatchSmem = 100 * 1024;  // float bytes of one batch (u and values, 32 lanes)
+constexpr int kSgsWaitLimit = 1 << 22;        // bounded wait for a batch's copies
+constexpr int kGatherRows = 8;                // rows per warp whose loads are issued together
 
 inline int grid_for(long long work, int cap) {
     long long g = (work + kBlock - 1) / kBlock;
@@ -184,86 +197,254 @@ __global__ void k_sgs_sweep(int ngroups, const int *__restrict__ hdr, const int 
     chk_report<CK>(bad, chk);
 }
 
-// 16-byte asynchronous copies of `bytes` (a multiple of 16, both addresses
-// 16-byte aligned) from global to shared memory by the 32 lanes of a warp
-__device__ __forceinline__ void stage_async(void *dst, const void *src, int bytes, int lane) {
-    const unsigned base = (unsigned)__cvta_generic_to_shared(dst);
-    const char *s = static_cast<const char *>(src);
-    for (int q = lane; 16 * q < bytes; q += 32)
-        asm volatile("cp.async.cg.shared.global [%0], [%1], 16;\n" ::"r"(base + 16 * q),
-                     "l"(s + 16 * q)
-                     : "memory");
-    asm volatile("cp.async.commit_group;\n" ::: "memory");
-}
-__device__ __forceinline__ void async_wait_all() {
-    asm volatile("cp.async.wait_group 0;\n" ::: "memory");
+// The C coupling terms of one row: acc - sum_k v_k u_(src_k), with the
+// coupling words (local row | value index << 16) read from shared memory as
+// warp-uniform (broadcast) loads; ul and svl are u and the values offset by
+// the lane.
+template <class T, int C, bool CK>
+__device__ __forceinline__ T row_terms(const unsigned *cw, const T *ul, const T *svl, T acc, int m,
+                                       int nv, int &bad) {
+    unsigned w[C];
+#pragma unroll
+    for (int k = 0; k < C; ++k) w[k] = cw[k];
+    T va[C], ua[C];
+#pragma unroll
+    for (int k = 0; k < C; ++k) {
+        va[k] = svl[32 * chk_index<CK>((int)(w[k] >> 16), nv, bad)];
+        ua[k] = ul[32 * chk_index<CK>((int)(w[k] & 0xffffu), m, bad)];
+    }
+#pragma unroll
+    for (int k = 0; k < C; ++k) acc = fmat(-va[k], ua[k], acc);
+    return acc;
 }
 
-// The batched sweep: 32 structurally identical groups of one column per
-// warp, one lane each.  The class structure (coupling pointers and local
-// indices, in row order) is the same for every lane and read as uniform
-// loads; each lane's u and coupling values sit in shared memory interleaved
-// by lane (row t of lane L at [32 t + L], conflict-free), the values of one
-// sweep at a time.  Each lane then sweeps its own block row by row, forward
-// and backward, with no synchronisation: no lane reads another lane's data.
-template <class T, bool CK = false>
-__global__ void k_sgs_batch(int nbatch, const int *__restrict__ bat_hdr,
-                            const int *__restrict__ cls_hdr,
-                            const unsigned short *__restrict__ cls_ptr,
-                            const unsigned short *__restrict__ cls_idx,
-                            const int *__restrict__ rpos, const T *__restrict__ fval,
-                            const T *__restrict__ bval, const T *__restrict__ R,
-                            T *__restrict__ Z, const DevState *st, int umax, int vmax, int *chk,
-                            long long ny) {
+// One level-ordered unit-diagonal triangular sweep of a batch held in u
+// (row t of lane L at u[32 t + L], conflict-free) with the coupling values
+// in sv (coupling o of lane L at sv[32 o + L]) and the class's sweep
+// structure in shared memory.  The rows of a level are spread over the
+// CTA's warps; a row's record (t | count << 10 | first coupling << 16) and
+// its couplings are the same for every lane.  Rows without couplings are not
+// listed.  One CTA barrier per level.
+template <class T, int NW, bool CK>
+__device__ __forceinline__ void batch_sweep(T *u, const T *sv, int nl, const unsigned *lvl,
+                                            const unsigned *rec, const unsigned *cpl, int nr,
+                                            int m, int nv, int warp, int lane, int &bad) {
+    T *ul = u + lane;
+    const T *svl = sv + lane;
+    for (int l = 0; l < nl; ++l) {
+        int a = (int)lvl[l], e = (int)lvl[l + 1];
+        if (CK && (a < 0 || e > nr || a > e)) {
+            bad = 1;
+            a = e = 0;
+        }
+        for (int x = a + warp; x < e; x += NW) {
+            const unsigned r = rec[x];
+            const int cnt = (int)((r >> 10) & 63u), c0 = (int)(r >> 16);
+            if (CK && c0 + cnt > nv) {
+                bad = 1;
+                continue;
+            }
+            const int t = chk_index<CK>((int)(r & 1023u), m, bad);
+            const unsigned *cw = cpl + c0;
+            T acc = ul[32 * t];
+            switch (cnt) {  // warp-uniform: exact unrolled paths for short rows
+                case 1: acc = row_terms<T, 1, CK>(cw, ul, svl, acc, m, nv, bad); break;
+                case 2: acc = row_terms<T, 2, CK>(cw, ul, svl, acc, m, nv, bad); break;
+                case 3: acc = row_terms<T, 3, CK>(cw, ul, svl, acc, m, nv, bad); break;
+                case 4: acc = row_terms<T, 4, CK>(cw, ul, svl, acc, m, nv, bad); break;
+                default: {
+                    int k = 0;
+                    for (; k + 4 <= cnt; k += 4)
+                        acc = row_terms<T, 4, CK>(cw + k, ul, svl, acc, m, nv, bad);
+                    for (; k < cnt; ++k) acc = row_terms<T, 1, CK>(cw + k, ul, svl, acc, m, nv, bad);
+                }
+            }
+            ul[32 * t] = acc;
+        }
+        __syncthreads();  // the next level reads this level's rows
+    }
+}
+
+// gamma modes of the batched sweep: none; this launch's block totals only
+// (an earlier bucket); block totals, then the grid total and the scalar step
+enum { SG_NONE = 0, SG_PART = 1, SG_LAST = 2 };
+
+// The batched sweep: one CTA per batch of 32 structurally identical
+// one-column groups (grid-stride over the bucket's batches).  Thread 0 posts
+// the batch's values (32 nv of them, contiguous) and, when the class
+// changes, the class's sweep structure on an mbarrier and brings both into
+// shared memory with TMA bulk copies while the warps gather r~ into u; then
+// the forward sweep, |u|^2 into gamma (SG_*), the backward sweep, and the
+// scatter of z~.  A lane without a group has positions -1, values 0 and
+// stays 0.
+template <class T, int NW, bool CK>
+__global__ void __launch_bounds__(NW * 32)
+k_sgs_batch(int b0, int b1, const int *__restrict__ bat_hdr, const int *__restrict__ cls_hdr,
+            const unsigned *__restrict__ cls_blob, const int *__restrict__ rpos,
+            const T *__restrict__ vals, const T *__restrict__ R, T *__restrict__ Z, DevState *st,
+            double *partials, int pbase, int gmode, int init, int umax, int vmax, int wmax,
+            int *chk, long long ny, long long nrpos, long long nval, long long nblob) {
     if (st->stop) return;
     int bad = 0;
     extern __shared__ __align__(16) unsigned char sgs_smem[];
-    const int lane = threadIdx.x & 31;
-    T *u = reinterpret_cast<T *>(sgs_smem) + (size_t)(threadIdx.x >> 5) * 32 * (umax + vmax);
-    T *sv = u + 32 * umax;
-    const int nwarps = (gridDim.x * blockDim.x) >> 5;
-    for (int b = (blockIdx.x * blockDim.x + threadIdx.x) >> 5; b < nbatch; b += nwarps) {
+    __shared__ __align__(8) unsigned long long bar;
+    __shared__ int s_abort;
+    __shared__ double sh[32];
+    T *u = reinterpret_cast<T *>(sgs_smem);
+    T *sv = u + 32 * (size_t)umax;
+    unsigned *sb = reinterpret_cast<unsigned *>(sv + 32 * (size_t)vmax);
+    const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
+    int cur_cls = -1;
+    if (tid == 0) {
+        mbar_init(&bar, 1);
+        fence_mbar_init();
+        s_abort = 0;
+    }
+    __syncthreads();
+    double g = 0.0;
+    unsigned phase = 0;
+    for (int b = b0 + blockIdx.x; b < b1; b += gridDim.x) {
         const int *h = bat_hdr + 4 * (size_t)b;
-        const int *ch = cls_hdr + 8 * (size_t)h[0];
-        const int m = ch[0], nf = ch[1], nb = ch[2];
-        const unsigned short *fp = cls_ptr + ch[3], *fi = cls_idx + ch[4];
-        const unsigned short *bp = cls_ptr + ch[5], *bi = cls_idx + ch[6];
-        const int *rp = rpos + h[1];
-        // the forward values in flight (16-byte asynchronous copies), then
-        // the gather of r~, then one wait
-        stage_async(sv, fval + h[2], 32 * nf * (int)sizeof(T), lane);
-#pragma unroll 8
-        for (int t = 0; t < m; ++t) {
-            const int p = rp[32 * t + lane];
-            u[32 * t + lane] = p >= 0 ? R[chk_index<CK>(p, ny, bad)] : T(0);
+        const int c = h[0], r0 = h[1], v0 = h[2];
+        const int *ch = cls_hdr + 8 * (size_t)c;
+        const int m = ch[0], nv = ch[1], nlf = ch[2], nlb = ch[3], off = ch[4], nrf = ch[5],
+                  nrb = ch[6], wpad = ch[7];
+        if constexpr (CK) {
+            // a batch whose header or class does not fit the arrays and the
+            // shared memory is skipped whole (the same test in every thread)
+            const long long words = (long long)nlf + 1 + nrf + nv + nlb + 1 + nrb + nv;
+            if (m < 0 || nv < 0 || nlf < 0 || nlb < 0 || nrf < 0 || nrb < 0 || off < 0 ||
+                (off & 3) || wpad < words || (wpad & 3) || wpad > wmax || r0 < 0 || v0 < 0 ||
+                m > umax || nv > vmax || off + wpad > nblob ||
+                (long long)r0 + 32LL * m > nrpos || (long long)v0 + 32LL * nv > nval) {
+                bad = 1;
+                continue;
+            }
         }
-        async_wait_all();
-        __syncwarp();
-        for (int t = 0; t < m; ++t) {
-            T acc = u[32 * t + lane];
-            const int o1 = fp[t + 1];
-            for (int o = fp[t]; o < o1; ++o)
-                acc = fmat(-sv[32 * o + lane], u[32 * chk_index<CK>(fi[o], m, bad) + lane], acc);
-            u[32 * t + lane] = acc;
+        // the class's sweep structure is copied only when it changes
+        const bool new_cls = c != cur_cls;
+        cur_cls = c;
+        if (tid == 0) {
+            fence_proxy_async();  // the previous batch's reads of sv and sb come first
+            const unsigned vbytes = 32u * (unsigned)nv * (unsigned)sizeof(T);
+            const unsigned wbytes = new_cls ? 4u * (unsigned)wpad : 0u;
+            mbar_expect_tx(&bar, vbytes + wbytes);
+            if (vbytes) bulk_g2s(sv, vals + v0, vbytes, &bar);
+            if (wbytes) bulk_g2s(sb, cls_blob + off, wbytes, &bar);
         }
-        __syncwarp();
-        stage_async(sv, bval + h[3], 32 * nb * (int)sizeof(T), lane);
-        async_wait_all();
-        __syncwarp();
-        for (int t = m - 1; t >= 0; --t) {
-            T acc = u[32 * t + lane];
-            const int o1 = bp[t + 1];
-            for (int o = bp[t]; o < o1; ++o)
-                acc = fmat(-sv[32 * o + lane], u[32 * chk_index<CK>(bi[o], m, bad) + lane], acc);
-            u[32 * t + lane] = acc;
+        // the gather of r~: each warp's rows in groups of kGatherRows, all
+        // their position loads, then all their loads of r~, in flight at once
+        for (int t0 = warp; t0 < m; t0 += kGatherRows * NW) {
+            int p[kGatherRows];
+#pragma unroll
+            for (int k = 0; k < kGatherRows; ++k) {
+                const int t = t0 + k * NW;
+                p[k] = t < m ? rpos[r0 + 32 * t + lane] : -1;
+            }
+            T v[kGatherRows];
+#pragma unroll
+            for (int k = 0; k < kGatherRows; ++k)
+                v[k] = p[k] >= 0 ? R[chk_index<CK>(p[k], ny, bad)] : T(0);
+#pragma unroll
+            for (int k = 0; k < kGatherRows; ++k) {
+                const int t = t0 + k * NW;
+                if (t < m) u[32 * t + lane] = v[k];
+            }
         }
-        for (int t = 0; t < m; ++t) {
-            const int p = rp[32 * t + lane];
-            if (p >= 0) Z[chk_index<CK>(p, ny, bad)] = u[32 * t + lane];
+        if (tid == 0 && !mbar_wait_bounded(&bar, phase, kSgsWaitLimit)) {
+            st->status = EMIN_ERR_TIMEOUT;
+            st->stop = 2;
+            mbar_wait_bounded(&bar, phase, kSgsWaitLimit);  // the copies in flight, bounded again
+            s_abort = 1;
         }
-        __syncwarp();  // the buffers are refilled by the warp's next batch
+        phase ^= 1u;
+        __syncthreads();
+        if (s_abort) break;
+        const unsigned *fl = sb;
+        const unsigned *fr = fl + nlf + 1, *fc = fr + nrf;
+        const unsigned *bl = fc + nv;
+        const unsigned *br = bl + nlb + 1, *bc = br + nrb;
+        batch_sweep<T, NW, CK>(u, sv, nlf, fl, fr, fc, nrf, m, nv, warp, lane, bad);
+        if (gmode != SG_NONE) {
+            // a thread's squares of one batch in T (a few dozen terms; the
+            // FP64 pipe is slow), then one double addition per batch
+            T gb = T(0);
+            for (int t = warp; t < m; t += NW) gb = fmat(u[32 * t + lane], u[32 * t + lane], gb);
+            g += (double)gb;
+            __syncthreads();  // every warp has read u before the backward sweep rewrites it
+        }
+        batch_sweep<T, NW, CK>(u, sv, nlb, bl, br, bc, nrb, m, nv, warp, lane, bad);
+        for (int t0 = warp; t0 < m; t0 += kGatherRows * NW) {
+            int p[kGatherRows];
+#pragma unroll
+            for (int k = 0; k < kGatherRows; ++k) {
+                const int t = t0 + k * NW;
+                p[k] = t < m ? rpos[r0 + 32 * t + lane] : -1;
+            }
+#pragma unroll
+            for (int k = 0; k < kGatherRows; ++k)
+                if (p[k] >= 0) Z[chk_index<CK>(p[k], ny, bad)] = u[32 * (t0 + k * NW) + lane];
+        }
+        __syncthreads();  // u, sv and sb are refilled by the next batch
     }
     chk_report<CK>(bad, chk);
+    if (gmode == SG_NONE) return;
+    const double bt = block_sum(g, sh);
+    if (gmode == SG_PART) {
+        if (tid == 0) partials[pbase + blockIdx.x] = bt;
+        return;
+    }
+    // the last bucket: the grid total over every bucket's block totals, in
+    // block order (deterministic), then gamma_0 or beta
+    __shared__ bool am_last;
+    if (tid == 0) {
+        partials[pbase + blockIdx.x] = bt;
+        __threadfence();
+        const unsigned t = atomicAdd(&st->ticket[1], 1u);
+        am_last = (t == gridDim.x - 1);
+    }
+    __syncthreads();
+    if (!am_last) return;
+    __threadfence();
+    double sum = 0.0;
+    for (int k = tid; k < pbase + (int)gridDim.x; k += blockDim.x) sum += __ldcg(partials + k);
+    sum = block_sum(sum, sh);
+    if (tid == 0) {
+        st->ticket[1] = 0u;
+        finalize_gamma(st, sum, init ? UPD_INIT : UPD_STEP, GammaFloor<T>::value);
+    }
+}
+
+// k = 1, fused SGS path: y~ = Pi z~ + beta y~ = z~ - q (q^T z~) + beta y~
+// per row (M >= the longest row of P held in registers; M = 0: any row).
+template <class T, int M>
+__global__ void __launch_bounds__(kBlock)
+k_ydir_proj_k1(int n, const int *__restrict__ Pp, const T *__restrict__ qv,
+               const T *__restrict__ Z, T *__restrict__ Y, const DevState *st) {
+    if (st->stop) return;
+    const T beta = (T)st->beta;
+    for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < n; i += gridDim.x * blockDim.x) {
+        const int p0 = Pp[i], p1 = Pp[i + 1];
+        if constexpr (M > 0) {
+            T q[M], z[M], y[M];
+            T t = T(0);
+#pragma unroll
+            for (int k = 0; k < M; ++k)
+                if (p0 + k < p1) {
+                    q[k] = qv[p0 + k];
+                    z[k] = Z[p0 + k];
+                    y[k] = Y[p0 + k];
+                    t = fmat(q[k], z[k], t);
+                }
+#pragma unroll
+            for (int k = 0; k < M; ++k)
+                if (p0 + k < p1) Y[p0 + k] = fmat(beta, y[k], fmat(-q[k], t, z[k]));
+        } else {
+            T t = T(0);
+            for (int s = p0; s < p1; ++s) t = fmat(qv[s], Z[s], t);
+            for (int s = p0; s < p1; ++s) Y[s] = fmat(beta, Y[s], fmat(-qv[s], t, Z[s]));
+        }
+    }
 }
 
 // k = 1: z~ <- Pi z~ = z~ - q (q^T z~) per row and gamma = <r~, z~> in one
@@ -425,7 +606,9 @@ int build_sgs_plan(int n, int nc, const int *Ap, const int *Aj, const int *Pp, c
         for (int t = 0; t < m; ++t) loc[L.rows[t]] = -1;
     };
     // phase 1: a structure hash of every group that could be batched (one
-    // column, at most kBatchRows rows)
+    // column, local rows and per-row coupling counts that fit the batched
+    // records, u, the values of 32 lanes and the sweep structure within
+    // kBatchSmem in float)
     std::vector<unsigned long long> ghash(ng, 0);
     std::vector<char> gelig(ng, 0);
     run([&](int tid) {
@@ -436,7 +619,15 @@ int build_sgs_plan(int n, int nc, const int *Ap, const int *Aj, const int *Pp, c
             const int m = colp[gcol[g] + 1] - colp[gcol[g]];
             if (gsize[g] != 1 || m > kBatchRows) continue;
             lists(g, loc, L);
-            if (L.nf > kBatchCouplings || L.nb > kBatchCouplings) continue;
+            if (128LL * (m + L.nf) + 4LL * (4LL * m + 2 * L.nf + 16) > kBatchSmem || L.nf > 65535)
+                continue;
+            std::vector<int> tcnt(m, 0);
+            bool fits = true;
+            for (int t = 0; t < m && fits; ++t) {
+                fits = (int)L.lo[t].size() <= kBatchRowCpl;
+                for (int v : L.lo[t]) fits = fits && ++tcnt[v] <= kBatchRowCpl;
+            }
+            if (!fits) continue;
             unsigned long long h = 1469598103934665603ULL;
             auto mix = [&](unsigned long long v) { h = (h ^ v) * 1099511628211ULL; };
             mix((unsigned long long)m);
@@ -451,7 +642,9 @@ int build_sgs_plan(int n, int nc, const int *Ap, const int *Aj, const int *Pp, c
         }
     });
     // phase 2: classes of structurally identical groups; a class with at
-    // least kBatchMin members is swept in batches of 32 (one lane a group)
+    // least kBatchMin members is batched, and so is every eligible class
+    // when the groups of the rarer ones are few (they then run beside the
+    // others instead of in a level-path launch of their own)
     out = SgsHost();
     std::unordered_map<unsigned long long, int> cls_of_hash;
     std::vector<int> gcls(ng, -1), cls_rep, cls_count;
@@ -470,26 +663,114 @@ int build_sgs_plan(int n, int nc, const int *Ap, const int *Aj, const int *Pp, c
         gcls[g] = c;
         cls_count[c]++;
     }
+    long long rare = 0;
+    for (size_t c = 0; c < cls_rep.size(); ++c)
+        if (cls_count[c] < kBatchMin) rare += cls_count[c];
+    const int min_count = rare <= kBatchTail ? 1 : kBatchMin;
     std::vector<int> bcls(cls_rep.size(), -1);  // class -> batched class index
     std::vector<Lists> canon;
     std::vector<int> gbatch(ng, -1), glane(ng, -1);
     {
         std::vector<int> loc(n, -1);
         std::vector<int> next(cls_rep.size(), 0);
+        std::vector<int> bc_src;  // batched class -> class
         for (size_t c = 0; c < cls_rep.size(); ++c) {
-            if (cls_count[c] < kBatchMin) continue;
+            if (cls_count[c] < min_count) continue;
             bcls[c] = (int)canon.size();
+            bc_src.push_back((int)c);
             canon.emplace_back();
             lists(cls_rep[c], loc, canon.back());
         }
-        // batches in group order within each class
-        std::vector<int> cls_first_batch(canon.size(), 0);
-        int nb_total = 0;
-        for (size_t c = 0; c < cls_rep.size(); ++c)
-            if (bcls[c] >= 0) {
-                cls_first_batch[bcls[c]] = nb_total;
-                nb_total += (cls_count[c] + 31) / 32;
+        const int nbc = (int)canon.size();
+        // buckets: the classes whose batch fits as many CTAs per SM as the
+        // class with the most groups, then the rest
+        auto foot = [&](int b) {
+            const long long m = (long long)canon[b].rows.size(), nv = canon[b].nf;
+            return 128LL * (m + nv) + 4LL * (4 * m + 2 * nv + 16);  // u, values, structure
+        };
+        auto per_sm = [](long long bytes) {
+            const long long cap = 228LL * 1024, per = bytes + 1024 + 512;
+            return std::min<long long>(2048 / (32 * kSgsWarps), cap / per);
+        };
+        std::vector<int> bucket_of(nbc, 0);
+        if (nbc > 0) {
+            int dom = 0;
+            for (int b = 1; b < nbc; ++b)
+                if (cls_count[bc_src[b]] > cls_count[bc_src[dom]]) dom = b;
+            long long fa = 0;
+            for (int b = 0; b < nbc; ++b)
+                if (per_sm(foot(b)) >= per_sm(foot(dom))) fa = std::max(fa, foot(b));
+            for (int b = 0; b < nbc; ++b) bucket_of[b] = foot(b) <= fa ? 0 : 1;
+        }
+        // class sweep structures: levels of the rows with couplings, row
+        // records and coupling words (see batch_sweep), 16-byte aligned and
+        // padded; value o of a class is its o-th lower coupling in row order
+        for (int b = 0; b < nbc; ++b) {
+            const Lists &L = canon[b];
+            const int m = (int)L.rows.size();
+            std::vector<int> fstart(m + 1, 0);
+            for (int t = 0; t < m; ++t) fstart[t + 1] = fstart[t] + (int)L.lo[t].size();
+            const int nv = fstart[m];
+            // the transpose: row t is coupled to the later rows u with t in lo[u]
+            std::vector<std::vector<std::pair<int, int>>> tr(m);
+            for (int t2 = 0; t2 < m; ++t2)
+                for (size_t x = 0; x < L.lo[t2].size(); ++x)
+                    tr[L.lo[t2][x]].push_back({t2, fstart[t2] + (int)x});
+            std::vector<int> fl(m, 0), bl(m, 0);
+            for (int t = 0; t < m; ++t)
+                for (int v : L.lo[t]) fl[t] = std::max(fl[t], fl[v] + 1);
+            for (int t = m - 1; t >= 0; --t)
+                for (auto &pr : tr[t]) bl[t] = std::max(bl[t], bl[pr.first] + 1);
+            while (out.cls_blob.size() % 4) out.cls_blob.push_back(0u);
+            const int off = (int)out.cls_blob.size();
+            int nl[2] = {0, 0}, nr[2] = {0, 0};
+            for (int sw = 0; sw < 2; ++sw) {
+                const std::vector<int> &lev = sw == 0 ? fl : bl;
+                int maxl = 0;
+                for (int t = 0; t < m; ++t) maxl = std::max(maxl, lev[t]);
+                std::vector<std::vector<int>> rows_at(maxl + 1);
+                for (int t = 0; t < m; ++t)
+                    if (lev[t] > 0) rows_at[lev[t]].push_back(t);
+                std::vector<unsigned> lvl, rec, cpl;
+                lvl.push_back(0);
+                for (int l = 1; l <= maxl; ++l) {
+                    for (int t : rows_at[l]) {
+                        const int cnt = sw == 0 ? (int)L.lo[t].size() : (int)tr[t].size();
+                        rec.push_back((unsigned)t | (unsigned)cnt << 10 | (unsigned)cpl.size() << 16);
+                        for (int x = 0; x < cnt; ++x) {
+                            const int src = sw == 0 ? L.lo[t][x] : tr[t][x].first;
+                            const int vi = sw == 0 ? fstart[t] + x : tr[t][x].second;
+                            cpl.push_back((unsigned)src | (unsigned)vi << 16);
+                        }
+                    }
+                    lvl.push_back((unsigned)rec.size());
+                }
+                nl[sw] = maxl;
+                nr[sw] = (int)rec.size();
+                for (auto *v : {&lvl, &rec, &cpl}) out.cls_blob.insert(out.cls_blob.end(), v->begin(), v->end());
             }
+            while (out.cls_blob.size() % 4) out.cls_blob.push_back(0u);
+            const int wpad = (int)out.cls_blob.size() - off;
+            const int h[8] = {m, nv, nl[0], nl[1], off, nr[0], nr[1], wpad};
+            out.cls_hdr.insert(out.cls_hdr.end(), h, h + 8);
+        }
+        // batches by bucket, then by class, groups in column order
+        std::vector<int> cls_first_batch(nbc, 0);
+        int nb_total = 0;
+        for (int bk = 0; bk < kSgsBuckets; ++bk) {
+            SgsBucket &B = out.bucket[bk];
+            B.b0 = nb_total;
+            for (int b = 0; b < nbc; ++b) {
+                if (bucket_of[b] != bk) continue;
+                cls_first_batch[b] = nb_total;
+                nb_total += (cls_count[bc_src[b]] + 31) / 32;
+                B.umax = std::max(B.umax, (int)canon[b].rows.size());
+                B.vmax = std::max(B.vmax, (int)canon[b].nf);
+                B.wmax = std::max(B.wmax, out.cls_hdr[8 * (size_t)b + 7]);
+            }
+            B.b1 = nb_total;
+        }
+        out.nbucket = out.bucket[1].b1 > out.bucket[1].b0 ? 2 : (nb_total > 0 ? 1 : 0);
         for (int g = 0; g < ng; ++g) {
             const int c = gcls[g];
             if (c < 0 || bcls[c] < 0) continue;
@@ -497,53 +778,28 @@ int build_sgs_plan(int n, int nc, const int *Ap, const int *Aj, const int *Pp, c
             gbatch[g] = cls_first_batch[bcls[c]] + k / 32;
             glane[g] = k % 32;
         }
-        // class structure: coupling pointers and local indices of both sweeps
-        for (size_t b = 0; b < canon.size(); ++b) {
-            const Lists &L = canon[b];
-            const int m = (int)L.rows.size();
-            const int h[8] = {m, (int)L.nf, (int)L.nb, (int)out.cls_ptr.size(), 0, 0, 0, 0};
-            out.cls_hdr.insert(out.cls_hdr.end(), h, h + 8);
-            int cp0 = (int)out.cls_ptr.size();
-            out.cls_hdr[8 * b + 3] = cp0;
-            out.cls_hdr[8 * b + 4] = (int)out.cls_idx.size();
-            int o = 0;
-            for (int t = 0; t < m; ++t) {
-                out.cls_ptr.push_back((unsigned short)o);
-                for (int v : L.lo[t]) out.cls_idx.push_back((unsigned short)v), ++o;
-            }
-            out.cls_ptr.push_back((unsigned short)o);
-            out.cls_hdr[8 * b + 5] = (int)out.cls_ptr.size();
-            out.cls_hdr[8 * b + 6] = (int)out.cls_idx.size();
-            o = 0;
-            for (int t = 0; t < m; ++t) {
-                out.cls_ptr.push_back((unsigned short)o);
-                for (int v : L.up[t]) out.cls_idx.push_back((unsigned short)v), ++o;
-            }
-            out.cls_ptr.push_back((unsigned short)o);
-            out.bmax_u = std::max(out.bmax_u, m);
-            out.bmax_v = std::max(out.bmax_v, (int)std::max(L.nf, L.nb));
-        }
         // batch headers and the lane arrays (empty lanes: position -1)
-        long long rp = 0, fv = 0, bv = 0;
-        for (size_t c = 0; c < cls_rep.size(); ++c) {
-            if (bcls[c] < 0) continue;
-            const Lists &L = canon[bcls[c]];
-            const int nbat = (cls_count[c] + 31) / 32;
-            for (int k = 0; k < nbat; ++k) {
-                const int h[4] = {bcls[c], (int)rp, (int)fv, (int)bv};
-                out.bat_hdr.insert(out.bat_hdr.end(), h, h + 4);
-                rp += 32LL * (long long)L.rows.size();
-                fv += 32LL * L.nf;
-                bv += 32LL * L.nb;
+        std::vector<int> bhdr(4LL * nb_total, 0);
+        long long rp = 0, fv = 0;
+        for (int bk = 0; bk < kSgsBuckets; ++bk)
+            for (int b = 0; b < nbc; ++b) {
+                if (bucket_of[b] != bk) continue;
+                const int nbat = (cls_count[bc_src[b]] + 31) / 32;
+                for (int k = 0; k < nbat; ++k) {
+                    int *hb = &bhdr[4 * (size_t)(cls_first_batch[b] + k)];
+                    hb[0] = b;
+                    hb[1] = (int)rp;
+                    hb[2] = (int)fv;
+                    rp += 32LL * (long long)canon[b].rows.size();
+                    fv += 32LL * canon[b].nf;
+                    if (rp > 0x7fffffffLL || fv > 0x7fffffffLL) return EMIN_ERR_ARG;
+                }
             }
-        }
-        if (rp > 0x7fffffffLL || fv > 0x7fffffffLL || bv > 0x7fffffffLL) return EMIN_ERR_ARG;
-        out.nbatch = (int)(out.bat_hdr.size() / 4);
+        out.bat_hdr.swap(bhdr);
+        out.nbatch = nb_total;
         out.bat_rpos.assign(rp, -1);
-        out.bat_fown.assign(fv, -1);
-        out.bat_fa.assign(fv, 0);
-        out.bat_bown.assign(bv, -1);
-        out.bat_ba.assign(bv, 0);
+        out.bat_own.assign(fv, -1);
+        out.bat_ent.assign(fv, 0);
     }
     // phase 3: batched groups fill their lane (after checking their lists
     // against the class's, so that equal hashes never stand in for equal
@@ -567,14 +823,8 @@ int build_sgs_plan(int n, int nc, const int *Ap, const int *Aj, const int *Pp, c
                     long long q = 0;
                     for (int t = 0; t < m; ++t)
                         for (size_t x = 0; x < L.lo[t].size(); ++x, ++q) {
-                            out.bat_fown[h[2] + 32 * q + lane] = L.rows[t];
-                            out.bat_fa[h[2] + 32 * q + lane] = L.lo_e[t][x];
-                        }
-                    q = 0;
-                    for (int t = 0; t < m; ++t)
-                        for (size_t x = 0; x < L.up[t].size(); ++x, ++q) {
-                            out.bat_bown[h[3] + 32 * q + lane] = L.rows[t];
-                            out.bat_ba[h[3] + 32 * q + lane] = L.up_e[t][x];
+                            out.bat_own[h[2] + 32 * q + lane] = L.rows[t];
+                            out.bat_ent[h[2] + 32 * q + lane] = L.lo_e[t][x];
                         }
                     continue;
                 }
@@ -701,46 +951,91 @@ void sweep_with(const Launch &L, const SgsOps<T> &s, const T *R, T *Z, const Dev
 }
 }  // namespace
 
-// Every warp owns a slot of at least 4 KB (8 KB for double) and at least the
-// largest u; groups that fit their slot whole are staged.  (Two groups per
-// warp on 16 lanes each was measured slower: different groups' level and
-// coupling counts make the two halves diverge.)
+namespace {
+// dynamic shared memory of a bucket's batched sweep: u and the values of 32
+// lanes, and the largest class sweep structure
 template <class T>
-void launch_sgs_sweep(const Launch &L, const SgsOps<T> &s, const T *R, T *Z, const DevState *st) {
-    if (s.nbatch > 0) {
-        // u and one sweep's values of 32 lanes per warp
-        const long long per_warp = 32LL * (s.bmax_u + s.bmax_v) * sizeof(T);
-        static bool attr = false;
-        if (!attr) {
-            cudaFuncSetAttribute(k_sgs_batch<T>, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                 200 * 1024);
-            cudaFuncSetAttribute(k_sgs_batch<T, true>, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                 200 * 1024);
-            cudaGetLastError();
-            attr = true;
-        }
-        long long wpb = (96 * 1024) / per_warp;
-        wpb = std::max(1LL, std::min(8LL, wpb));
-        const int threads = (int)(32 * wpb);
-        const size_t smem = (size_t)(wpb * per_warp);
-        int per_sm = 1;
-        if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_sgs_batch<T>, threads, smem) !=
-                cudaSuccess ||
-            per_sm < 1) {
-            cudaGetLastError();
-            per_sm = 1;
-        }
-        long long blocks = ((long long)s.nbatch + wpb - 1) / wpb;
-        blocks = std::min(blocks, (long long)L.nsm * per_sm);
+size_t batch_smem(const SgsBucket &B) {
+    return (size_t)32 * (size_t)(B.umax + B.vmax) * sizeof(T) + 4 * (size_t)B.wmax;
+}
+
+// dynamic shared memory a batched sweep may use: a float batch is kept
+// within kBatchSmem, a double one within twice that (and the structure)
+constexpr int kBatchSmemOptIn = 2 * (int)kBatchSmem + 16 * 1024;
+
+template <class T>
+bool batch_attributes() {
+    static int done = 0;  // 1 set, -1 refused
+    if (!done) {
+        const bool ok = cudaFuncSetAttribute(k_sgs_batch<T, kSgsWarps, false>,
+                                             cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                             kBatchSmemOptIn) == cudaSuccess &&
+                        cudaFuncSetAttribute(k_sgs_batch<T, kSgsWarps, true>,
+                                             cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                             kBatchSmemOptIn) == cudaSuccess;
+        cudaGetLastError();
+        done = ok ? 1 : -1;
+    }
+    return done > 0;
+}
+
+// CTAs of one bucket (at most its batches, at most what fits every SM);
+// -1 when the shared-memory opt-in was refused
+template <class T>
+int batch_grid(int nsm, const SgsBucket &B) {
+    const int nb = B.b1 - B.b0;
+    if (nb <= 0) return 0;
+    if (!batch_attributes<T>()) return -1;
+    int per_sm = 0;
+    if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_sgs_batch<T, kSgsWarps, false>,
+                                                      32 * kSgsWarps, batch_smem<T>(B)) !=
+            cudaSuccess ||
+        per_sm < 1) {
+        cudaGetLastError();
+        return -1;
+    }
+    return (int)std::min<long long>(nb, (long long)nsm * per_sm);
+}
+}  // namespace
+
+// CTAs of every bucket for both value types (the plan keeps a float batch
+// within kBatchSmem, so the double one, twice as large, fits one CTA too)
+int sgs_prepare(int nsm, SgsHost &h) {
+    for (int b = 0; b < h.nbucket; ++b) {
+        SgsBucket &B = h.bucket[b];
+        if (batch_smem<double>(B) > (size_t)kBatchSmemOptIn) return EMIN_ERR_ARG;
+        B.grid32 = batch_grid<float>(nsm, B);
+        B.grid64 = batch_grid<double>(nsm, B);
+        if (B.b1 > B.b0 && (B.grid32 < 1 || B.grid64 < 1)) return EMIN_ERR_CUDA;
+    }
+    return EMIN_OK;
+}
+
+// The batched buckets first (with s.fused, gamma over all of them: block
+// totals of the earlier buckets in the partials, the grid total and the
+// scalar step in the last), then the level path.
+template <class T>
+void launch_sgs_sweep(const Launch &L, const SgsOps<T> &s, const T *R, T *Z, DevState *st,
+                      double *partials, int init) {
+    int pbase = 0;
+    for (int b = 0; b < s.nbucket; ++b) {
+        const SgsBucket &B = s.bucket[b];
+        const int grid = sizeof(T) == 4 ? B.grid32 : B.grid64;
+        if (grid <= 0) continue;
+        const int gmode = !s.fused ? SG_NONE : (b == s.nbucket - 1 ? SG_LAST : SG_PART);
+        const size_t smem = batch_smem<T>(B);
         if (s.chk)
-            k_sgs_batch<T, true><<<(int)blocks, threads, smem, L.stream>>>(
-                s.nbatch, s.bat_hdr, s.cls_hdr, s.cls_ptr, s.cls_idx, s.bat_rpos, s.bat_fval,
-                s.bat_bval, R, Z, st, s.bmax_u, s.bmax_v, s.chk, s.ny);
+            k_sgs_batch<T, kSgsWarps, true><<<grid, 32 * kSgsWarps, smem, L.stream>>>(
+                B.b0, B.b1, s.bat_hdr, s.cls_hdr, s.cls_blob, s.bat_rpos, s.bat_val, R, Z, st,
+                partials, pbase, gmode, init, B.umax, B.vmax, B.wmax, s.chk, s.ny, s.nbat_rpos,
+                s.nbat_val, s.ncls_blob);
         else
-            k_sgs_batch<T><<<(int)blocks, threads, smem, L.stream>>>(
-                s.nbatch, s.bat_hdr, s.cls_hdr, s.cls_ptr, s.cls_idx, s.bat_rpos, s.bat_fval,
-                s.bat_bval, R, Z, st, s.bmax_u, s.bmax_v, nullptr, s.ny);
+            k_sgs_batch<T, kSgsWarps, false><<<grid, 32 * kSgsWarps, smem, L.stream>>>(
+                B.b0, B.b1, s.bat_hdr, s.cls_hdr, s.cls_blob, s.bat_rpos, s.bat_val, R, Z, st,
+                partials, pbase, gmode, init, B.umax, B.vmax, B.wmax, nullptr, s.ny,
+                s.nbat_rpos, s.nbat_val, s.ncls_blob);
         note_launch();
+        pbase += grid;
     }
     if (s.ngroups > 0) {
         const long long ubytes = ((long long)s.cap * sizeof(T) + 15) / 16 * 16;
@@ -751,6 +1046,20 @@ void launch_sgs_sweep(const Launch &L, const SgsOps<T> &s, const T *R, T *Z, con
             sweep_with<T, kSgsMaxCols, 32>(L, s, R, Z, st, slot);
         note_launch();
     }
+}
+
+template <class T>
+void launch_ydir_proj_k1(const Launch &L, int n, int maxrow, const int *Pp, const T *qv,
+                         const T *Z, T *Y, const DevState *st) {
+    if (n <= 0) return;
+    const int g = grid_for(n, L.grid_rows);
+    if (maxrow <= 4)
+        k_ydir_proj_k1<T, 4><<<g, kBlock, 0, L.stream>>>(n, Pp, qv, Z, Y, st);
+    else if (maxrow <= 8)
+        k_ydir_proj_k1<T, 8><<<g, kBlock, 0, L.stream>>>(n, Pp, qv, Z, Y, st);
+    else
+        k_ydir_proj_k1<T, 0><<<g, kBlock, 0, L.stream>>>(n, Pp, qv, Z, Y, st);
+    note_launch();
 }
 
 // k = 1: projection and gamma in one pass; otherwise projection, then gamma
@@ -773,9 +1082,13 @@ template void launch_sgs_values<double>(const Launch &, const int *, const int *
                                         const int *, const int *, long long, const int *,
                                         const double *, const double *, double *, double *);
 template void launch_sgs_sweep<float>(const Launch &, const SgsOps<float> &, const float *,
-                                      float *, const DevState *);
+                                      float *, DevState *, double *, int);
 template void launch_sgs_sweep<double>(const Launch &, const SgsOps<double> &, const double *,
-                                       double *, const DevState *);
+                                       double *, DevState *, double *, int);
+template void launch_ydir_proj_k1<float>(const Launch &, int, int, const int *, const float *,
+                                         const float *, float *, const DevState *);
+template void launch_ydir_proj_k1<double>(const Launch &, int, int, const int *, const double *,
+                                          const double *, double *, const DevState *);
 template void launch_sgs_finish<float>(const Launch &, const Ops<float> &, Work<float> &, int,
                                        long long);
 template void launch_sgs_finish<double>(const Launch &, const Ops<double> &, Work<double> &, int,
