@@ -47,7 +47,7 @@ constexpr int kBatchMin = 8;          // groups of one structure before it is ba
 constexpr int kBatchTail = 1024;      // rarer structures batched too while this few groups have them
 constexpr long long kBatchSmem = 100 * 1024;  // float bytes of one batch (u and values, 32 lanes)
 constexpr int kSgsWaitLimit = 1 << 22;        // bounded wait for a batch's copies
-constexpr int kGatherRows = 8;                // rows per warp whose loads are issued together
+constexpr int kGatherRows = 16;               // rows per warp whose loads are issued together
 
 inline int grid_for(long long work, int cap) {
     long long g = (work + kBlock - 1) / kBlock;
@@ -197,6 +197,19 @@ __global__ void k_sgs_sweep(int ngroups, const int *__restrict__ hdr, const int 
     chk_report<CK>(bad, chk);
 }
 
+// 4-byte (float) or 8-byte (double) asynchronous copy global -> shared,
+// completed by cp_async_wait_all in the issuing thread
+template <class T>
+__device__ __forceinline__ void cp_async4(T *dst, const T *src) {
+    static_assert(sizeof(T) == 4 || sizeof(T) == 8, "cp.async of 4 or 8 bytes");
+    asm volatile("cp.async.ca.shared.global [%0], [%1], %2;\n" ::"r"(smem_addr(dst)), "l"(src),
+                 "n"((int)sizeof(T))
+                 : "memory");
+}
+__device__ __forceinline__ void cp_async_wait_all() {
+    asm volatile("cp.async.wait_all;\n" ::: "memory");
+}
+
 // The C coupling terms of one row: acc - sum_k v_k u_(src_k), with the
 // coupling words (local row | value index << 16) read from shared memory as
 // warp-uniform (broadcast) loads; ul and svl are u and the values offset by
@@ -333,24 +346,25 @@ k_sgs_batch(int b0, int b1, const int *__restrict__ bat_hdr, const int *__restri
             if (wbytes) bulk_g2s(sb, cls_blob + off, wbytes, &bar);
         }
         // the gather of r~: each warp's rows in groups of kGatherRows, all
-        // their position loads, then all their loads of r~, in flight at once
+        // their position loads in flight at once, then asynchronous copies
+        // of r~ straight into u (no register round trip, all in flight)
         for (int t0 = warp; t0 < m; t0 += kGatherRows * NW) {
             int p[kGatherRows];
 #pragma unroll
             for (int k = 0; k < kGatherRows; ++k) {
                 const int t = t0 + k * NW;
-                p[k] = t < m ? rpos[r0 + 32 * t + lane] : -1;
+                p[k] = t < m ? rpos[r0 + 32 * t + lane] : -2;
             }
-            T v[kGatherRows];
-#pragma unroll
-            for (int k = 0; k < kGatherRows; ++k)
-                v[k] = p[k] >= 0 ? R[chk_index<CK>(p[k], ny, bad)] : T(0);
 #pragma unroll
             for (int k = 0; k < kGatherRows; ++k) {
-                const int t = t0 + k * NW;
-                if (t < m) u[32 * t + lane] = v[k];
+                T *dst = u + 32 * (t0 + k * NW) + lane;
+                if (p[k] >= 0)
+                    cp_async4(dst, R + chk_index<CK>(p[k], ny, bad));
+                else if (p[k] == -1)
+                    *dst = T(0);  // a lane without a group
             }
         }
+        cp_async_wait_all();
         if (tid == 0 && !mbar_wait_bounded(&bar, phase, kSgsWaitLimit)) {
             st->status = EMIN_ERR_TIMEOUT;
             st->stop = 2;
@@ -379,7 +393,7 @@ k_sgs_batch(int b0, int b1, const int *__restrict__ bat_hdr, const int *__restri
 #pragma unroll
             for (int k = 0; k < kGatherRows; ++k) {
                 const int t = t0 + k * NW;
-                p[k] = t < m ? rpos[r0 + 32 * t + lane] : -1;
+                p[k] = t < m ? rpos[r0 + 32 * t + lane] : -2;
             }
 #pragma unroll
             for (int k = 0; k < kGatherRows; ++k)
