@@ -81,6 +81,18 @@ __host__ __device__ __forceinline__ long long tile_len16(int W, int npairs, int 
     return v.bc16 + ((long long)naggs * kBStride * sizeof(T) + 15) / 16;
 }
 
+// a pair of T (8 or 16 bytes), the unit of the blob's paired values
+template <class T>
+struct PairOf;
+template <>
+struct PairOf<float> {
+    using V = float2;
+};
+template <>
+struct PairOf<double> {
+    using V = double2;
+};
+
 // ---------------------------------------------------------------------------
 // Values of the blob, refreshed at every set-up: A^ = D^-1/2 A D^-1/2 (dsq
 // null: A itself) in pairs, Ginv and B_c in the working precision.
@@ -98,26 +110,40 @@ k_nbs_fill(long long npairs, const int4 *__restrict__ fp, long long nnodes,
     for (long long q = blockIdx.x * (long long)blockDim.x + threadIdx.x; q < total;
          q += (long long)gridDim.x * blockDim.x) {
         if (q < npairs) {
+            // a node-blocked row stores neighbour j's 3 x 3 block at columns
+            // NB j .. NB j + 2 of each of the node's rows, all in the column
+            // node b: one read of Aj per neighbour, D^-1/2 of b's three dofs
+            // shared by the three rows
             const int4 f = fp[q];
             const int v = f.x, j0 = f.y;
             const int a0 = Ap[NB * v], rs = Ap[NB * v + 1] - a0;
-            T *dst = blob + (unsigned)f.z;
+            using V = typename PairOf<T>::V;
+            V *dst = reinterpret_cast<V *>(blob + (unsigned)f.z);
+            double dv[NB], db[2][NB], a[2][NB][NB];
+#pragma unroll
+            for (int r = 0; r < NB; ++r) dv[r] = dsq ? dsq[NB * v + r] : 1.0;
 #pragma unroll
             for (int h = 0; h < 2; ++h) {
                 const int j = j0 + h;
                 const bool has = h == 0 || f.w;
+                const int cb = has ? Aj[a0 + NB * j] : 0;  // first column of node b
+#pragma unroll
+                for (int c = 0; c < NB; ++c) db[h][c] = (has && dsq) ? dsq[cb + c] : 1.0;
 #pragma unroll
                 for (int r = 0; r < NB; ++r)
 #pragma unroll
-                    for (int c = 0; c < NB; ++c) {
-                        double a = 0.0;
-                        if (has) {
-                            const int e = a0 + r * rs + NB * j + c;
-                            a = dsq ? dsq[NB * v + r] * Av[e] * dsq[Aj[e]] : Av[e];
-                        }
-                        dst[(r * NB + c) * 2 + h] = (T)a;
-                    }
+                    for (int c = 0; c < NB; ++c)
+                        a[h][r][c] = has ? Av[a0 + r * rs + NB * j + c] : 0.0;
             }
+#pragma unroll
+            for (int r = 0; r < NB; ++r)
+#pragma unroll
+                for (int c = 0; c < NB; ++c) {
+                    V u;
+                    u.x = (T)(dv[r] * a[0][r][c] * db[0][c]);
+                    u.y = (T)(dv[r] * a[1][r][c] * db[1][c]);
+                    dst[r * NB + c] = u;
+                }
         } else if (q < npairs + nnodes) {
             const int2 f = fnode[q - npairs];
             const double *g = Ginv + (size_t)NB * f.x * KK;
@@ -154,16 +180,6 @@ __device__ __forceinline__ void lds_row6(const double *p, double (&y)[KB]) {
     }
 }
 
-template <class T>
-struct PairOf;
-template <>
-struct PairOf<float> {
-    using V = float2;
-};
-template <>
-struct PairOf<double> {
-    using V = double2;
-};
 
 // ---------------------------------------------------------------------------
 // The staged product.  Dynamic shared memory: [blob cap][Y cap][scratch

@@ -130,12 +130,57 @@ __device__ void pinv_sym(double (&G)[K * K], double (&out)[K * K]) {
     }
 }
 
+// G_i = B_i^T B_i (B_i = Bc(J_i,:)), full, for the rank-deficient rows
+template <int K>
+__device__ __forceinline__ void gram_full(int p0, int p1, const int *__restrict__ Pj,
+                                          const double *__restrict__ Bc, double (&G)[K * K]) {
+#pragma unroll
+    for (int a = 0; a < K * K; ++a) G[a] = 0.0;
+    for (int s = p0; s < p1; ++s) {
+        const double *b = Bc + (size_t)Pj[s] * K;
+#pragma unroll
+        for (int a = 0; a < K; ++a)
+#pragma unroll
+            for (int c = 0; c < K; ++c) G[a * K + c] = fma(b[a], b[c], G[a * K + c]);
+    }
+}
+
+// The rows whose G_i failed the rank test: the pseudo-inverse (counted) or
+// an error and a zero factor.  Kept out of line: it is rare, and its
+// dense arrays would otherwise weigh on the registers of every row.
+template <int K>
+__device__ __noinline__ void gram_rank_deficient(int i, int rep, int p0, int p1,
+                                                 const int *__restrict__ Pj,
+                                                 const double *__restrict__ Bc, double *Ginv,
+                                                 float *Ginv32, int policy, int *flags,
+                                                 int *ndef) {
+    constexpr int KK = K * (K + 1) / 2;
+    double out[K * K];
+    if (policy == EMIN_RANK_PINV) {
+        double G[K * K];
+        gram_full<K>(p0, p1, Pj, Bc, G);
+        pinv_sym<K>(G, out);
+        atomicAdd(ndef, rep);
+    } else {
+        atomicOr(flags, F_RANK);
+        for (int a = 0; a < K * K; ++a) out[a] = 0.0;
+    }
+    for (int r = 0; r < rep; ++r)
+        for (int a = 0; a < K; ++a)
+            for (int b = 0; b <= a; ++b) {
+                Ginv[(size_t)(i + r) * KK + tri(a, b)] = out[a * K + b];
+                Ginv32[(size_t)(i + r) * KK + tri(a, b)] = (float)out[a * K + b];
+            }
+}
+
 // Per row: G_i = B_i^T B_i (B_i = Bc(J_i,:)) in double, Cholesky G = L L^T
 // with the rank test L_jj^2 <= tol * max diag(G_i), then G_i^{-1} = L^{-T}
 // L^{-1} stored packed.  Rank-deficient rows: error (strict) or the
-// pseudo-inverse (counted).
+// pseudo-inverse (counted).  Every matrix is held as its packed lower
+// triangle, the factor overwriting G, with one reciprocal per pivot.
 template <int K>
-__global__ void k_gram(int n, const int *__restrict__ Pp, const int *__restrict__ Pj,
+__global__ void __launch_bounds__(kBlock, K >= 6 ? 3 : 1)
+k_gram(int n, const int *__restrict__ Pp, const int *__restrict__ Pj,
                        const double *__restrict__ Bc, double *Ginv, float *Ginv32, int policy,
                        int *flags, int *ndef, int rep) {
     // rep consecutive rows share their columns of P (rep = 3 for the rows of
@@ -144,9 +189,9 @@ __global__ void k_gram(int n, const int *__restrict__ Pp, const int *__restrict_
     const int ngr = n / rep;
     for (int gi = blockIdx.x * blockDim.x + threadIdx.x; gi < ngr; gi += gridDim.x * blockDim.x) {
         const int i = gi * rep;
-        double G[K * K];
+        double G[KK];
 #pragma unroll
-        for (int a = 0; a < K * K; ++a) G[a] = 0.0;
+        for (int a = 0; a < KK; ++a) G[a] = 0.0;
         const int p0 = Pp[i], p1 = Pp[i + 1];
         for (int s = p0; s < p1; ++s) {
             const double *b = Bc + (size_t)Pj[s] * K;
@@ -156,75 +201,57 @@ __global__ void k_gram(int n, const int *__restrict__ Pp, const int *__restrict_
 #pragma unroll
             for (int a = 0; a < K; ++a)
 #pragma unroll
-                for (int c = 0; c <= a; ++c) G[a * K + c] = fma(bv[a], bv[c], G[a * K + c]);
+                for (int c = 0; c <= a; ++c) G[tri(a, c)] = fma(bv[a], bv[c], G[tri(a, c)]);
         }
         double maxd = 0.0;
 #pragma unroll
-        for (int a = 0; a < K; ++a) maxd = fmax(maxd, G[a * K + a]);
-        double L[K * K];
-#pragma unroll
-        for (int a = 0; a < K * K; ++a) L[a] = 0.0;
+        for (int a = 0; a < K; ++a) maxd = fmax(maxd, G[tri(a, a)]);
         bool ok = (p1 - p0 >= K) && maxd > 0.0;
+        double rinv[K];  // 1 / L_jj
 #pragma unroll
         for (int j = 0; j < K; ++j) {
-            double d = G[j * K + j];
+            double d = G[tri(j, j)];
 #pragma unroll
-            for (int q = 0; q < j; ++q) d -= L[j * K + q] * L[j * K + q];
+            for (int q = 0; q < j; ++q) d -= G[tri(j, q)] * G[tri(j, q)];
             if (!(d > kRankTol * maxd)) ok = false;
             const double ljj = sqrt(fmax(d, 1e-300));
-            L[j * K + j] = ljj;
+            rinv[j] = 1.0 / ljj;
+            G[tri(j, j)] = ljj;
 #pragma unroll
             for (int r = j + 1; r < K; ++r) {
-                double v = G[r * K + j];
+                double v = G[tri(r, j)];
 #pragma unroll
-                for (int q = 0; q < j; ++q) v -= L[r * K + q] * L[j * K + q];
-                L[r * K + j] = v / ljj;
+                for (int q = 0; q < j; ++q) v -= G[tri(r, q)] * G[tri(j, q)];
+                G[tri(r, j)] = v * rinv[j];
             }
         }
-        double out[K * K];
-        if (ok) {
-            // Li = L^{-1} (lower), then G^{-1} = Li^T Li
-            double Li[K * K];
-#pragma unroll
-            for (int a = 0; a < K * K; ++a) Li[a] = 0.0;
-#pragma unroll
-            for (int c = 0; c < K; ++c)
-#pragma unroll
-                for (int a = c; a < K; ++a) {
-                    double v = (a == c) ? 1.0 : 0.0;
-#pragma unroll
-                    for (int q = c; q < a; ++q) v -= L[a * K + q] * Li[q * K + c];
-                    Li[a * K + c] = v / L[a * K + a];
-                }
-#pragma unroll
-            for (int a = 0; a < K; ++a)
-#pragma unroll
-                for (int b = 0; b <= a; ++b) {
-                    double v = 0.0;
-#pragma unroll
-                    for (int q = a; q < K; ++q) v += Li[q * K + a] * Li[q * K + b];
-                    out[a * K + b] = v;
-                }
-        } else if (policy == EMIN_RANK_PINV) {
-#pragma unroll
-            for (int a = 0; a < K; ++a)
-#pragma unroll
-                for (int b = 0; b < a; ++b) G[b * K + a] = G[a * K + b];
-            pinv_sym<K>(G, out);
-            atomicAdd(ndef, rep);
-        } else {
-            atomicOr(flags, F_RANK);
-#pragma unroll
-            for (int a = 0; a < K * K; ++a) out[a] = 0.0;
+        if (!ok) {
+            gram_rank_deficient<K>(i, rep, p0, p1, Pj, Bc, Ginv, Ginv32, policy, flags, ndef);
+            continue;
         }
-        for (int r = 0; r < rep; ++r)
+        // Li = L^{-1} (lower), then G^{-1} = Li^T Li
+        double Li[KK];
 #pragma unroll
-            for (int a = 0; a < K; ++a)
+        for (int c = 0; c < K; ++c)
 #pragma unroll
-                for (int b = 0; b <= a; ++b) {
-                    Ginv[(size_t)(i + r) * KK + tri(a, b)] = out[a * K + b];
-                    Ginv32[(size_t)(i + r) * KK + tri(a, b)] = (float)out[a * K + b];
+            for (int a = c; a < K; ++a) {
+                double v = (a == c) ? 1.0 : 0.0;
+#pragma unroll
+                for (int q = c; q < a; ++q) v -= G[tri(a, q)] * Li[tri(q, c)];
+                Li[tri(a, c)] = v * rinv[a];
+            }
+#pragma unroll
+        for (int a = 0; a < K; ++a)
+#pragma unroll
+            for (int b = 0; b <= a; ++b) {
+                double v = 0.0;
+#pragma unroll
+                for (int q = a; q < K; ++q) v += Li[tri(q, a)] * Li[tri(q, b)];
+                for (int r = 0; r < rep; ++r) {
+                    Ginv[(size_t)(i + r) * KK + tri(a, b)] = v;
+                    Ginv32[(size_t)(i + r) * KK + tri(a, b)] = (float)v;
                 }
+            }
     }
 }
 
