@@ -147,6 +147,7 @@ std::vector<void *> g_host_blocks;  // recycled pinned blocks (kHostBlock bytes)
 constexpr size_t kHostBlock = 256;
 constexpr size_t kHintOffset = 128;
 constexpr int kHintChk = 8;  // the mirror of the check word: hint[kHintChk]
+constexpr int kHintTotal = 10;  // a 64-bit count read back at creation: hint[10..11]
 static_assert(sizeof(DevState) <= kHintOffset, "state mirror overlaps the flag mirror");
 
 cudaMemPool_t device_pool(int dev) {
@@ -783,21 +784,19 @@ int create_impl(emin_ctx *c, const int *A_rowptr, const int *A_col, const double
         const int ns = (n + 31) / 32;
         EMIN_TRY(dalloc(c, &c->sell_ptr, ns + 1));
         launch_sell_len(c->L, n, c->Ap, c->sell_ptr);
-        std::vector<int> h(ns + 1, 0);
-        EMIN_TRY(cuda_status(cudaMemcpyAsync(h.data(), c->sell_ptr, sizeof(int) * ns,
+        // slice starts by a scan on the device; only the entry count comes
+        // back (no upload that would queue behind the value copies)
+        long long *dtotal = nullptr;
+        EMIN_TRY(dalloc(c, &dtotal, 1));
+        launch_sell_scan(c->L, ns, c->sell_ptr, dtotal);
+        long long *htotal = reinterpret_cast<long long *>(c->hint + kHintTotal);
+        EMIN_TRY(cuda_status(cudaMemcpyAsync(htotal, dtotal, sizeof(long long),
                                              cudaMemcpyDeviceToHost, c->stream)));
         EMIN_TRY(sync(c));
-        long long acc = 0;
-        for (int s = 0; s < ns; ++s) {
-            const long long len = h[s];
-            h[s] = (int)acc;
-            acc += 32 * len;
-        }
+        const long long acc = *htotal;
+        dfree(c, dtotal);
         if (acc > 0x7fffffffLL) return EMIN_ERR_ARG;
-        h[ns] = (int)acc;
         c->nnz_sell = acc;
-        EMIN_TRY(cuda_status(cudaMemcpyAsync(c->sell_ptr, h.data(), sizeof(int) * (ns + 1),
-                                             cudaMemcpyHostToDevice, c->stream)));
         EMIN_TRY(dalloc(c, &c->soff, acc));
         EMIN_TRY(dalloc(c, &c->smap, acc));
         EMIN_TRY(dalloc(c, &c->sw, acc));
@@ -807,7 +806,7 @@ int create_impl(emin_ctx *c, const int *A_rowptr, const int *A_col, const double
                          c->sw, c->dint + 3, c->dpos, acc, c->opts.checks ? c->chkw : nullptr);
         EMIN_TRY(cuda_status(cudaMemcpyAsync(c->hint + 3, c->dint + 3, sizeof(int),
                                              cudaMemcpyDeviceToHost, c->stream)));
-        EMIN_TRY(sync(c));  // the host copy of the offsets must outlive the transfer
+        EMIN_TRY(sync(c));  // the plan's verdict (do the offsets fit the packed word?)
         // the packed plan when every offset difference fits its word, else the plain one
         if (c->hint[3] == 0) {
             dfree(c, c->soff);

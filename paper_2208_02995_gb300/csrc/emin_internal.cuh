@@ -262,6 +262,8 @@ void launch_final_k1(const Launch &L, int n, const int *Pp, const int *Pj, const
 // SELL-32 plan: slice lengths (longest row of A per 32 rows), then the plan
 // in slice order once sell_ptr (exclusive scan of 32 * length) is known
 void launch_sell_len(const Launch &L, int n, const int *Ap, int *slen);
+// slice lengths -> slice starts in place, the entry count into *total (device)
+void launch_sell_scan(const Launch &L, int ns, int *sptr, long long *total);
 // sw may be null (no packed words); *wide is set when an offset difference
 // does not fit the packed word
 void launch_sell_plan(const Launch &L, int n, const int *Ap, const int *Aj, const int *Pp,

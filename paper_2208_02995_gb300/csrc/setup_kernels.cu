@@ -518,6 +518,37 @@ __global__ void k_sell_len(int n, const int *__restrict__ Ap, int *slen) {
     }
 }
 
+// slice lengths -> slice starts in place (exclusive prefix sum of 32 len),
+// one block: each thread scans a contiguous run, the run totals are scanned
+// across the block; *total receives the plan's entry count (64-bit, so
+// that the host can reject a plan beyond int32 positions)
+__global__ void __launch_bounds__(1024) k_sell_scan(int ns, int *sptr, long long *total) {
+    __shared__ long long part[1024];
+    const int t = threadIdx.x, per = (ns + 1023) / 1024;
+    const int b0 = min(ns, t * per), b1 = min(ns, b0 + per);
+    long long sum = 0;
+    for (int s = b0; s < b1; ++s) sum += 32LL * sptr[s];
+    part[t] = sum;
+    __syncthreads();
+    for (int off = 1; off < 1024; off <<= 1) {  // inclusive scan of the run totals
+        const long long v = t >= off ? part[t - off] : 0;
+        __syncthreads();
+        part[t] += v;
+        __syncthreads();
+    }
+    long long acc = part[t] - sum;
+    for (int s = b0; s < b1; ++s) {
+        const long long len = 32LL * sptr[s];
+        // positions past int32 are never used: the host rejects such a plan
+        sptr[s] = (int)(acc < 0x7fffffffLL ? acc : 0x7fffffffLL);
+        acc += len;
+    }
+    if (t == 1023) {
+        sptr[ns] = (int)(part[1023] < 0x7fffffffLL ? part[1023] : 0x7fffffffLL);
+        *total = part[1023];
+    }
+}
+
 // The k = 1 plan of the fixed pattern (the adjacency of Section 4, built
 // once) in SELL-32 order: for every stored (i, l) of A, the offset of row l
 // of P and, for each slot s < 4 of row i, the position q of the same column
@@ -776,6 +807,11 @@ template void launch_final_k1<double>(const Launch &, int, const int *, const in
                                       const double *, const double *, const double *,
                                       const double *, const double *, const double *, int,
                                       double *);
+
+void launch_sell_scan(const Launch &L, int ns, int *sptr, long long *total) {
+    k_sell_scan<<<1, 1024, 0, L.stream>>>(ns, sptr, total);
+    note_launch();
+}
 
 void launch_sell_len(const Launch &L, int n, const int *Ap, int *slen) {
     if (n <= 0) return;
