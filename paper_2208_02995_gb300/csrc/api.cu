@@ -96,6 +96,7 @@ struct emin_ctx {
     int applied_seen = 0;
     std::vector<void *> dev_allocs;
     cudaMemPool_t pool = nullptr;  // stream-ordered pool of dev_allocs (null: cudaMalloc)
+    void *host_dev = nullptr;      // the pinned host block's device mapping (null: none)
     // create from host arrays: the value arrays are copied on a second
     // stream while the context's stream validates the pattern and builds
     // the plan
@@ -273,6 +274,28 @@ int copy_out(emin_ctx *c, void *dst, const void *src, size_t bytes, int on_devic
 }
 
 int sync(emin_ctx *c) { return cuda_status(cudaStreamSynchronize(c->stream)); }
+
+__global__ void k_fetch_words(const unsigned *__restrict__ src, unsigned *dst, int nwords) {
+    for (int i = threadIdx.x; i < nwords; i += blockDim.x) dst[i] = src[i];
+}
+
+// A few words of device memory into the context's pinned host block: stored
+// by a one-warp kernel through the block's device mapping when there is one
+// (no copy engine, so the read does not wait behind bulk host-to-device
+// copies in flight on another stream), else by cudaMemcpyAsync.  Complete
+// after the next sync.
+int fetch_words(emin_ctx *c, void *hdst, const void *dsrc, size_t bytes) {
+    const size_t off = (size_t)(static_cast<char *>(hdst) - static_cast<char *>(c->host_blk));
+    if (c->host_dev && bytes % 4 == 0 && off + bytes <= kHostBlock &&
+        reinterpret_cast<uintptr_t>(dsrc) % 4 == 0) {
+        unsigned *d = reinterpret_cast<unsigned *>(static_cast<char *>(c->host_dev) + off);
+        k_fetch_words<<<1, 32, 0, c->stream>>>(static_cast<const unsigned *>(dsrc), d,
+                                               (int)(bytes / 4));
+        note_launch();
+        return check_launch();
+    }
+    return cuda_status(cudaMemcpyAsync(hdst, dsrc, bytes, cudaMemcpyDeviceToHost, c->stream));
+}
 
 // masked products on the unscaled A (energy, adjoint right-hand sides)
 // bounds checks of the kernels (emin_opts.checks)
@@ -620,8 +643,7 @@ int run_setup(emin_ctx *c) {
 }
 
 int read_flags(emin_ctx *c) {
-    EMIN_TRY(cuda_status(cudaMemcpyAsync(c->hint, c->dint, 3 * sizeof(int), cudaMemcpyDeviceToHost,
-                                         c->stream)));
+    EMIN_TRY(fetch_words(c, c->hint, c->dint, 3 * sizeof(int)));
     EMIN_TRY(sync(c));
     const int f = c->hint[0];
     c->ndef = c->hint[2];
@@ -727,6 +749,10 @@ int create_impl(emin_ctx *c, const int *A_rowptr, const int *A_col, const double
     if (!c->host_blk) return EMIN_ERR_NOMEM;
     c->hstate = static_cast<DevState *>(c->host_blk);
     c->hint = reinterpret_cast<int *>(static_cast<char *>(c->host_blk) + kHintOffset);
+    if (cudaHostGetDevicePointer(&c->host_dev, c->host_blk, 0) != cudaSuccess) {
+        cudaGetLastError();
+        c->host_dev = nullptr;
+    }
 
     // the patterns first, on the context's stream
     EMIN_TRY(copy_in(c, c->Ap, A_rowptr, sizeof(int) * (n + 1), on_dev));
@@ -756,11 +782,24 @@ int create_impl(emin_ctx *c, const int *A_rowptr, const int *A_col, const double
         return cuda_status(cudaMemcpyAsync(
             dst, src, bytes, on_dev ? cudaMemcpyDeviceToDevice : cudaMemcpyHostToDevice, cs));
     };
-    EMIN_TRY(copy_values(c->Av, A_val, sizeof(double) * c->nnz_a));
+    // The value arrays cross the link while the patterns are checked and
+    // planned: P0, B and B_c right behind the patterns, A's values (the
+    // largest) once the plan's arrays are allocated.  An allocation or free
+    // from the pool blocks the host while a transfer is in flight, so every
+    // allocation of the plan is made while only the small arrays travel and
+    // the unused ones are freed after the set-up (`late`).
     EMIN_TRY(copy_values(c->P0_in, P0_val, sizeof(double) * c->nnz_p));
     EMIN_TRY(copy_values(c->B, B, sizeof(double) * nk));
     EMIN_TRY(copy_values(c->Bc, Bc, sizeof(double) * nck));
-    if (split) EMIN_TRY(cuda_status(cudaEventRecord(c->side_ev, c->side)));
+    bool av_issued = false;
+    auto issue_av = [&]() -> int {
+        if (av_issued) return EMIN_OK;
+        av_issued = true;
+        EMIN_TRY(copy_values(c->Av, A_val, sizeof(double) * c->nnz_a));
+        if (split) EMIN_TRY(cuda_status(cudaEventRecord(c->side_ev, c->side)));
+        return EMIN_OK;
+    };
+    void *late[2] = {nullptr, nullptr};
 
     // validate the patterns on the device before any kernel indexes through
     // them (the values are checked once they have arrived, below; their
@@ -769,8 +808,7 @@ int create_impl(emin_ctx *c, const int *A_rowptr, const int *A_col, const double
     launch_validate_csr(c->L, n, n, c->Ap, (int)c->nnz_a, c->Aj, c->dint, c->dint + 3);
     launch_validate_csr(c->L, n, c->nc, c->Pp, (int)c->nnz_p, c->Pj, c->dint, c->dint + 1);
     EMIN_TRY(check_launch());
-    EMIN_TRY(cuda_status(cudaMemcpyAsync(c->hint, c->dint, 4 * sizeof(int), cudaMemcpyDeviceToHost,
-                                         c->stream)));
+    EMIN_TRY(fetch_words(c, c->hint, c->dint, 4 * sizeof(int)));
     EMIN_TRY(sync(c));
     const int f = c->hint[0];
     if (f & (F_ROWPTR | F_COL | F_ORDER)) return EMIN_ERR_PATTERN;
@@ -790,8 +828,7 @@ int create_impl(emin_ctx *c, const int *A_rowptr, const int *A_col, const double
         EMIN_TRY(dalloc(c, &dtotal, 1));
         launch_sell_scan(c->L, ns, c->sell_ptr, dtotal);
         long long *htotal = reinterpret_cast<long long *>(c->hint + kHintTotal);
-        EMIN_TRY(cuda_status(cudaMemcpyAsync(htotal, dtotal, sizeof(long long),
-                                             cudaMemcpyDeviceToHost, c->stream)));
+        EMIN_TRY(fetch_words(c, htotal, dtotal, sizeof(long long)));
         EMIN_TRY(sync(c));
         const long long acc = *htotal;
         dfree(c, dtotal);
@@ -801,34 +838,44 @@ int create_impl(emin_ctx *c, const int *A_rowptr, const int *A_col, const double
         EMIN_TRY(dalloc(c, &c->smap, acc));
         EMIN_TRY(dalloc(c, &c->sw, acc));
         EMIN_TRY(dalloc(c, &c->dpos, n));
-        EMIN_TRY(cuda_status(cudaMemsetAsync(c->dint + 3, 0, sizeof(int), c->stream)));
-        launch_sell_plan(c->L, n, c->Ap, c->Aj, c->Pp, c->Pj, c->sell_ptr, c->soff, c->smap,
-                         c->sw, c->dint + 3, c->dpos, acc, c->opts.checks ? c->chkw : nullptr);
-        EMIN_TRY(cuda_status(cudaMemcpyAsync(c->hint + 3, c->dint + 3, sizeof(int),
-                                             cudaMemcpyDeviceToHost, c->stream)));
-        EMIN_TRY(sync(c));  // the plan's verdict (do the offsets fit the packed word?)
-        // the packed plan when every offset difference fits its word, else the plain one
-        if (c->hint[3] == 0) {
-            dfree(c, c->soff);
-            dfree(c, c->smap);
-        } else {
-            dfree(c, c->sw);
-        }
+        // A^ in plan order: packed records (float) or values (double); a float
+        // plan that turns out plain takes its values in a smaller array below
         if (c->opts.precision == EMIN_MIXED) {
             EMIN_TRY(dalloc(c, &c->dsq32, n));
-            if (c->sw) EMIN_TRY(dalloc(c, &c->spk32, acc));
-            else EMIN_TRY(dalloc(c, &c->sa32, acc));
+            EMIN_TRY(dalloc(c, &c->spk32, acc));
         } else {
             EMIN_TRY(dalloc(c, &c->sa64, acc));
         }
+        EMIN_TRY(issue_av());
+        EMIN_TRY(cuda_status(cudaMemsetAsync(c->dint + 3, 0, sizeof(int), c->stream)));
+        launch_sell_plan(c->L, n, c->Ap, c->Aj, c->Pp, c->Pj, c->sell_ptr, c->soff, c->smap,
+                         c->sw, c->dint + 3, c->dpos, acc, c->opts.checks ? c->chkw : nullptr);
+        EMIN_TRY(fetch_words(c, c->hint + 3, c->dint + 3, sizeof(int)));
+        EMIN_TRY(sync(c));  // the plan's verdict (do the offsets fit the packed word?)
+        // the packed plan when every offset difference fits its word, else the
+        // plain one; the arrays of the other are freed after the set-up
+        if (c->hint[3] == 0) {
+            late[0] = c->soff;
+            late[1] = c->smap;
+            c->soff = nullptr;
+            c->smap = nullptr;
+        } else {
+            late[0] = c->sw;
+            c->sw = nullptr;
+            if (c->opts.precision == EMIN_MIXED) {
+                late[1] = c->spk32;
+                c->spk32 = nullptr;
+                EMIN_TRY(dalloc(c, &c->sa32, acc));
+            }
+        }
     }
+    EMIN_TRY(issue_av());
 
     if (!c->fast_k1) {
         // node-blocked problems (elasticity): plan of 3 x 3 / 3 x 6 blocks
         EMIN_TRY(cuda_status(cudaMemsetAsync(c->dint + 3, 0, sizeof(int), c->stream)));
         if (launch_detect_blocks(c->L, n, c->k, c->Ap, c->Aj, c->Pp, c->Pj, c->dint + 3)) {
-            EMIN_TRY(cuda_status(cudaMemcpyAsync(c->hint + 3, c->dint + 3, sizeof(int),
-                                                 cudaMemcpyDeviceToHost, c->stream)));
+            EMIN_TRY(fetch_words(c, c->hint + 3, c->dint + 3, sizeof(int)));
             EMIN_TRY(sync(c));
             if (c->hint[3] == 0) {
                 const long long ne = block_plan_entries(c->nnz_a);
@@ -907,6 +954,7 @@ int create_impl(emin_ctx *c, const int *A_rowptr, const int *A_col, const double
     launch_check_finite(c->L, c->Bc, nck, c->dint);
     EMIN_TRY(check_launch());
     EMIN_TRY(read_flags(c));
+    for (void *p : late) dfree(c, p);
     return with_checks(c, EMIN_OK);
 }
 

@@ -519,33 +519,58 @@ __global__ void k_sell_len(int n, const int *__restrict__ Ap, int *slen) {
 }
 
 // slice lengths -> slice starts in place (exclusive prefix sum of 32 len),
-// one block: each thread scans a contiguous run, the run totals are scanned
-// across the block; *total receives the plan's entry count (64-bit, so
-// that the host can reject a plan beyond int32 positions)
+// one block of 1024 threads over tiles of 4096 slices: each tile is read
+// with coalesced loads, every thread scans 4 consecutive slices, the thread
+// totals are scanned across the block (warp shuffles, then the 32 warp
+// totals), and the running total carries to the next tile; *total receives
+// the plan's entry count (64-bit, so that the host can reject a plan beyond
+// int32 positions)
 __global__ void __launch_bounds__(1024) k_sell_scan(int ns, int *sptr, long long *total) {
-    __shared__ long long part[1024];
-    const int t = threadIdx.x, per = (ns + 1023) / 1024;
-    const int b0 = min(ns, t * per), b1 = min(ns, b0 + per);
-    long long sum = 0;
-    for (int s = b0; s < b1; ++s) sum += 32LL * sptr[s];
-    part[t] = sum;
-    __syncthreads();
-    for (int off = 1; off < 1024; off <<= 1) {  // inclusive scan of the run totals
-        const long long v = t >= off ? part[t - off] : 0;
+    __shared__ long long wsum[32];
+    __shared__ long long carry_s;
+    const int t = threadIdx.x, lane = t & 31, w = t >> 5;
+    long long carry = 0;
+    for (int base = 0; base < ns; base += 4096) {
+        long long v[4], run = 0;
+#pragma unroll
+        for (int k = 0; k < 4; ++k) {
+            const int s = base + 4 * t + k;
+            v[k] = s < ns ? 32LL * sptr[s] : 0;
+            run += v[k];
+        }
+        long long inc = run;  // inclusive scan of the thread totals in the warp
+#pragma unroll
+        for (int o = 1; o < 32; o <<= 1) {
+            const long long u = __shfl_up_sync(0xffffffffu, inc, o);
+            if (lane >= o) inc += u;
+        }
+        if (lane == 31) wsum[w] = inc;
         __syncthreads();
-        part[t] += v;
+        if (w == 0) {
+            long long x = wsum[lane], xi = x;
+#pragma unroll
+            for (int o = 1; o < 32; o <<= 1) {
+                const long long u = __shfl_up_sync(0xffffffffu, xi, o);
+                if (lane >= o) xi += u;
+            }
+            wsum[lane] = xi - x;  // exclusive over the warps
+            if (lane == 31) carry_s = xi;
+        }
         __syncthreads();
+        long long acc = carry + wsum[w] + inc - run;
+#pragma unroll
+        for (int k = 0; k < 4; ++k) {
+            const int s = base + 4 * t + k;
+            // positions past int32 are never used: the host rejects such a plan
+            if (s < ns) sptr[s] = (int)(acc < 0x7fffffffLL ? acc : 0x7fffffffLL);
+            acc += v[k];
+        }
+        carry += carry_s;
+        __syncthreads();  // wsum and carry_s are rewritten by the next tile
     }
-    long long acc = part[t] - sum;
-    for (int s = b0; s < b1; ++s) {
-        const long long len = 32LL * sptr[s];
-        // positions past int32 are never used: the host rejects such a plan
-        sptr[s] = (int)(acc < 0x7fffffffLL ? acc : 0x7fffffffLL);
-        acc += len;
-    }
-    if (t == 1023) {
-        sptr[ns] = (int)(part[1023] < 0x7fffffffLL ? part[1023] : 0x7fffffffLL);
-        *total = part[1023];
+    if (t == 0) {
+        sptr[ns] = (int)(carry < 0x7fffffffLL ? carry : 0x7fffffffLL);
+        *total = carry;
     }
 }
 
