@@ -75,8 +75,6 @@ struct emin_ctx {
     unsigned *sgs_cls_blob = nullptr;
     float *sgs_batval32 = nullptr;
     double *sgs_batval64 = nullptr;
-    cudaStream_t sgs_side = nullptr;  // the second bucket's stream (see sgs.cu)
-    cudaEvent_t sgs_fork = nullptr, sgs_join = nullptr;
     float *sgs_fval32 = nullptr, *sgs_bval32 = nullptr;
     double *sgs_fval64 = nullptr, *sgs_bval64 = nullptr;
     double *Pstar = nullptr, *t64c = nullptr;
@@ -348,9 +346,6 @@ SgsOps<T> sgs_ops(const emin_ctx *c, const T *fval, const T *bval, const T *batv
     s.fval = fval;
     s.bval = bval;
     s.fused = c->k == 1 && qv != nullptr && c->sgs_ngroups == 0 && c->sgs_nbatch > 0;
-    s.side = c->sgs_side;
-    s.fork = c->sgs_fork;
-    s.join = c->sgs_join;
     return s;
 }
 
@@ -544,11 +539,6 @@ int build_sgs(emin_ctx *c) {
     }
     c->sgs_nbatch = h.nbatch;
     c->sgs_nbucket = h.nbucket;
-    if (h.nbucket == 2) {  // the buckets run side by side
-        EMIN_TRY(cuda_status(cudaStreamCreateWithFlags(&c->sgs_side, cudaStreamNonBlocking)));
-        EMIN_TRY(cuda_status(cudaEventCreateWithFlags(&c->sgs_fork, cudaEventDisableTiming)));
-        EMIN_TRY(cuda_status(cudaEventCreateWithFlags(&c->sgs_join, cudaEventDisableTiming)));
-    }
     for (int b = 0; b < kSgsBuckets; ++b) c->sgs_bucket[b] = h.bucket[b];
     EMIN_TRY(upload(c, &c->sgs_cls_hdr, h.cls_hdr));
     EMIN_TRY(upload(c, &c->sgs_bat_hdr, h.bat_hdr));
@@ -1154,7 +1144,6 @@ void emin_destroy(emin_ctx *c) {
     {
         DeviceGuard g(c->device);
         if (c->side) cudaStreamSynchronize(c->side);
-        if (c->sgs_side) cudaStreamSynchronize(c->sgs_side);
         cudaStreamSynchronize(c->stream);
         for (cudaGraphExec_t g : {c->w64.gexec, c->adj.gexec, c->aux.gexec})
             if (g) cudaGraphExecDestroy(g);
@@ -1166,9 +1155,6 @@ void emin_destroy(emin_ctx *c) {
         host_block_put(c->host_blk);
         if (c->side_ev) cudaEventDestroy(c->side_ev);
         if (c->side) cudaStreamDestroy(c->side);
-        for (cudaEvent_t e : {c->sgs_fork, c->sgs_join})
-            if (e) cudaEventDestroy(e);
-        if (c->sgs_side) cudaStreamDestroy(c->sgs_side);
         cudaGetLastError();
     }
     delete c;

@@ -124,9 +124,6 @@ struct SgsOps {
     // gamma formed by the batched sweep and the projection applied in the
     // direction update (k = 1, every group batched)
     bool fused = false;
-    // the second bucket runs beside the first on this stream (null: after it)
-    cudaStream_t side = nullptr;
-    cudaEvent_t fork = nullptr, join = nullptr;
     int ngroups = 0;
     int cap = 0;                 // largest m * G
     int gmax = 0;                // largest G

@@ -278,21 +278,24 @@ __device__ __forceinline__ void batch_sweep(T *u, const T *sv, int nl, const uns
     }
 }
 
+// gamma modes of the batched sweep: none; this launch's block totals only
+// (an earlier bucket); block totals, then the grid total and the scalar step
+enum { SG_NONE = 0, SG_PART = 1, SG_LAST = 2 };
 
 // The batched sweep: one CTA per batch of 32 structurally identical
 // one-column groups (grid-stride over the bucket's batches).  Thread 0 posts
 // the batch's values (32 nv of them, contiguous) and, when the class
 // changes, the class's sweep structure on an mbarrier and brings both into
 // shared memory with TMA bulk copies while the warps gather r~ into u; then
-// the forward sweep, |u|^2 into gamma (ptotal > 0), the backward sweep, and
-// the scatter of z~.  A lane without a group has positions -1, values 0 and
+// the forward sweep, |u|^2 into gamma (SG_*), the backward sweep, and the
+// scatter of z~.  A lane without a group has positions -1, values 0 and
 // stays 0.
 template <class T, int NW, bool CK>
 __global__ void __launch_bounds__(NW * 32)
 k_sgs_batch(int b0, int b1, const int *__restrict__ bat_hdr, const int *__restrict__ cls_hdr,
             const unsigned *__restrict__ cls_blob, const int *__restrict__ rpos,
             const T *__restrict__ vals, const T *__restrict__ R, T *__restrict__ Z, DevState *st,
-            double *partials, int pbase, int ptotal, int init, int umax, int vmax, int wmax,
+            double *partials, int pbase, int gmode, int init, int umax, int vmax, int wmax,
             int *chk, long long ny, long long nrpos, long long nval, long long nblob) {
     if (st->stop) return;
     int bad = 0;
@@ -376,7 +379,7 @@ k_sgs_batch(int b0, int b1, const int *__restrict__ bat_hdr, const int *__restri
         const unsigned *bl = fc + nv;
         const unsigned *br = bl + nlb + 1, *bc = br + nrb;
         batch_sweep<T, NW, CK>(u, sv, nlf, fl, fr, fc, nrf, m, nv, warp, lane, bad);
-        if (ptotal > 0) {
+        if (gmode != SG_NONE) {
             // a thread's squares of one batch in T (a few dozen terms; the
             // FP64 pipe is slow), then one double addition per batch
             T gb = T(0);
@@ -399,24 +402,26 @@ k_sgs_batch(int b0, int b1, const int *__restrict__ bat_hdr, const int *__restri
         __syncthreads();  // u, sv and sb are refilled by the next batch
     }
     chk_report<CK>(bad, chk);
-    if (ptotal <= 0) return;
-    // gamma over the CTAs of every bucket's launch (which may run at the same
-    // time): each writes its block total at pbase + its index, the last of
-    // all ptotal to arrive sums them in index order (deterministic), then
-    // gamma_0 or beta
+    if (gmode == SG_NONE) return;
     const double bt = block_sum(g, sh);
+    if (gmode == SG_PART) {
+        if (tid == 0) partials[pbase + blockIdx.x] = bt;
+        return;
+    }
+    // the last bucket: the grid total over every bucket's block totals, in
+    // block order (deterministic), then gamma_0 or beta
     __shared__ bool am_last;
     if (tid == 0) {
         partials[pbase + blockIdx.x] = bt;
         __threadfence();
         const unsigned t = atomicAdd(&st->ticket[1], 1u);
-        am_last = (t == (unsigned)ptotal - 1u);
+        am_last = (t == gridDim.x - 1);
     }
     __syncthreads();
     if (!am_last) return;
     __threadfence();
     double sum = 0.0;
-    for (int k = tid; k < ptotal; k += blockDim.x) sum += __ldcg(partials + k);
+    for (int k = tid; k < pbase + (int)gridDim.x; k += blockDim.x) sum += __ldcg(partials + k);
     sum = block_sum(sum, sh);
     if (tid == 0) {
         st->ticket[1] = 0u;
@@ -1020,45 +1025,31 @@ int sgs_prepare(int nsm, SgsHost &h) {
     return EMIN_OK;
 }
 
-// The batched buckets first (with s.fused, gamma over all of them), then the
-// level path.  With two buckets and a side stream, the second bucket (few,
-// large batches: one latency-bound wave) is launched first on the side
-// stream and the first bucket beside it, joined before the level path.
+// The batched buckets first (with s.fused, gamma over all of them: block
+// totals of the earlier buckets in the partials, the grid total and the
+// scalar step in the last), then the level path.
 template <class T>
 void launch_sgs_sweep(const Launch &L, const SgsOps<T> &s, const T *R, T *Z, DevState *st,
                       double *partials, int init) {
-    int grid[kSgsBuckets] = {0, 0}, pbase[kSgsBuckets] = {0, 0}, ptotal = 0;
+    int pbase = 0;
     for (int b = 0; b < s.nbucket; ++b) {
-        grid[b] = sizeof(T) == 4 ? s.bucket[b].grid32 : s.bucket[b].grid64;
-        pbase[b] = ptotal;
-        ptotal += grid[b] > 0 ? grid[b] : 0;
-    }
-    if (!s.fused) ptotal = 0;
-    auto launch = [&](int b, cudaStream_t stream) {
         const SgsBucket &B = s.bucket[b];
-        if (grid[b] <= 0) return;
+        const int grid = sizeof(T) == 4 ? B.grid32 : B.grid64;
+        if (grid <= 0) continue;
+        const int gmode = !s.fused ? SG_NONE : (b == s.nbucket - 1 ? SG_LAST : SG_PART);
         const size_t smem = batch_smem<T>(B);
         if (s.chk)
-            k_sgs_batch<T, kSgsWarps, true><<<grid[b], 32 * kSgsWarps, smem, stream>>>(
+            k_sgs_batch<T, kSgsWarps, true><<<grid, 32 * kSgsWarps, smem, L.stream>>>(
                 B.b0, B.b1, s.bat_hdr, s.cls_hdr, s.cls_blob, s.bat_rpos, s.bat_val, R, Z, st,
-                partials, pbase[b], ptotal, init, B.umax, B.vmax, B.wmax, s.chk, s.ny,
-                s.nbat_rpos, s.nbat_val, s.ncls_blob);
+                partials, pbase, gmode, init, B.umax, B.vmax, B.wmax, s.chk, s.ny, s.nbat_rpos,
+                s.nbat_val, s.ncls_blob);
         else
-            k_sgs_batch<T, kSgsWarps, false><<<grid[b], 32 * kSgsWarps, smem, stream>>>(
+            k_sgs_batch<T, kSgsWarps, false><<<grid, 32 * kSgsWarps, smem, L.stream>>>(
                 B.b0, B.b1, s.bat_hdr, s.cls_hdr, s.cls_blob, s.bat_rpos, s.bat_val, R, Z, st,
-                partials, pbase[b], ptotal, init, B.umax, B.vmax, B.wmax, nullptr, s.ny,
+                partials, pbase, gmode, init, B.umax, B.vmax, B.wmax, nullptr, s.ny,
                 s.nbat_rpos, s.nbat_val, s.ncls_blob);
         note_launch();
-    };
-    if (s.nbucket == 2 && grid[0] > 0 && grid[1] > 0 && s.side && s.fork && s.join) {
-        cudaEventRecord(s.fork, L.stream);
-        cudaStreamWaitEvent(s.side, s.fork, 0);
-        launch(1, s.side);
-        launch(0, L.stream);
-        cudaEventRecord(s.join, s.side);
-        cudaStreamWaitEvent(L.stream, s.join, 0);
-    } else {
-        for (int b = 0; b < s.nbucket; ++b) launch(b, L.stream);
+        pbase += grid;
     }
     if (s.ngroups > 0) {
         const long long ubytes = ((long long)s.cap * sizeof(T) + 15) / 16 * 16;
