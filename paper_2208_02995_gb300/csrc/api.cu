@@ -75,6 +75,7 @@ struct emin_ctx {
     unsigned *sgs_cls_blob = nullptr;
     float *sgs_batval32 = nullptr;
     double *sgs_batval64 = nullptr;
+    bool sgs_sellpos = false;  // bat_ent holds plan positions (values read from A^ in plan order)
     float *sgs_fval32 = nullptr, *sgs_bval32 = nullptr;
     double *sgs_fval64 = nullptr, *sgs_bval64 = nullptr;
     double *Pstar = nullptr, *t64c = nullptr;
@@ -547,6 +548,11 @@ int build_sgs(emin_ctx *c) {
     EMIN_TRY(upload(c, &c->sgs_bat_ent, h.bat_ent));
     EMIN_TRY(upload(c, &c->sgs_cls_blob, h.cls_blob));
     c->sgs_nbval = (long long)h.bat_ent.size();
+    if (c->sell_ptr && c->sgs_nbval > 0) {
+        launch_sgs_sell_pos(c->L, c->sgs_nbval, c->sgs_bat_own, c->sgs_bat_ent, c->Ap,
+                            c->sell_ptr);
+        c->sgs_sellpos = true;
+    }
     c->sgs_nbrpos = (long long)h.bat_rpos.size();
     c->sgs_ncls_blob = (long long)h.cls_blob.size();
     const long long nf = (long long)h.fa.size(), nb = (long long)h.ba.size();
@@ -571,8 +577,17 @@ void form_sgs_values(emin_ctx *c, T *fval, T *bval, T *batval) {
     if (c->opts.precond != EMIN_SGS) return;
     launch_sgs_values<T>(c->L, c->sgs_fown, c->sgs_fa, c->sgs_nf, c->sgs_bown, c->sgs_ba,
                          c->sgs_nb, c->Aj, c->Av, c->dsq, fval, bval);
-    launch_sgs_values<T>(c->L, c->sgs_bat_own, c->sgs_bat_ent, c->sgs_nbval, nullptr, nullptr, 0,
-                         c->Aj, c->Av, c->dsq, batval, nullptr);
+    if (c->sgs_sellpos) {  // A^ in plan order was formed just before, in this precision
+        if constexpr (sizeof(T) == 4)
+            launch_sgs_values_sell<float>(c->L, c->sgs_nbval, c->sgs_bat_own, c->sgs_bat_ent,
+                                          c->sa32, c->spk32, batval);
+        else
+            launch_sgs_values_sell<double>(c->L, c->sgs_nbval, c->sgs_bat_own, c->sgs_bat_ent,
+                                           c->sa64, nullptr, batval);
+    } else {
+        launch_sgs_values<T>(c->L, c->sgs_bat_own, c->sgs_bat_ent, c->sgs_nbval, nullptr, nullptr,
+                             0, c->Aj, c->Av, c->dsq, batval, nullptr);
+    }
 }
 
 // A^ and q in double (the FP64 path, or the adjoint of a mixed context)

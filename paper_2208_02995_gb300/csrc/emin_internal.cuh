@@ -331,6 +331,13 @@ template <class T>
 void launch_sgs_values(const Launch &L, const int *fown, const int *fa, long long nf,
                        const int *bown, const int *ba, long long nb, const int *Aj,
                        const double *Av, const double *dsq, T *fval, T *bval);
+// with the packed k = 1 plan: the batched couplings' A entries turned into
+// plan positions (once), and their values read from A^ in plan order
+void launch_sgs_sell_pos(const Launch &L, long long nops, const int *own, int *ent,
+                         const int *Ap, const int *sell_ptr);
+template <class T>
+void launch_sgs_values_sell(const Launch &L, long long nops, const int *own, const int *pos,
+                            const T *sa, const uint2 *spk, T *val);
 // z~ <- Pi z~ and gamma = <r~, z~> after the sweep (init: gamma_0)
 template <class T>
 void launch_sgs_finish(const Launch &L, const Ops<T> &o, Work<T> &w, int init, long long nnz_p);

@@ -77,6 +77,40 @@ __global__ void k_sgs_values(long long nops, const int *__restrict__ own,
     }
 }
 
+// With the packed k = 1 plan (SELL-32 order of A), A^ is already formed in
+// plan order at every set-up; the batched couplings then read it there.
+// Their A entries become plan positions once per context: entry e of row i
+// sits at the slice start + 32 (e - Ap[i]) + i mod 32.  Lanes without a
+// group (own < 0) are left as they are.
+__global__ void k_sgs_sell_pos(long long nops, const int *__restrict__ own, int *ent,
+                               const int *__restrict__ Ap, const int *__restrict__ sell_ptr) {
+    for (long long o = blockIdx.x * (long long)blockDim.x + threadIdx.x; o < nops;
+         o += (long long)gridDim.x * blockDim.x) {
+        const int i = own[o];
+        if (i < 0) continue;
+        ent[o] = sell_ptr[i >> 5] + 32 * (ent[o] - Ap[i]) + (i & 31);
+    }
+}
+
+// A^ at the batched couplings from A^ in plan order: the value half of a
+// packed record (float, spk) or the plain array (sa); 0 on empty lanes
+template <class T>
+__global__ void k_sgs_values_sell(long long nops, const int *__restrict__ own,
+                                  const int *__restrict__ pos, const T *__restrict__ sa,
+                                  const uint2 *__restrict__ spk, T *__restrict__ val) {
+    for (long long o = blockIdx.x * (long long)blockDim.x + threadIdx.x; o < nops;
+         o += (long long)gridDim.x * blockDim.x) {
+        T v = T(0);
+        if (own[o] >= 0) {
+            if constexpr (sizeof(T) == 4)
+                v = spk ? __uint_as_float(spk[pos[o]].x) : sa[pos[o]];
+            else
+                v = sa[pos[o]];
+        }
+        val[o] = v;
+    }
+}
+
 // Group header (12 ints): rows m, columns G, first plan row r0, index blob
 // offset and length (16-byte units), first forward / backward value,
 // forward / backward couplings nf / nb, forward / backward levels.
@@ -925,6 +959,28 @@ void launch_sgs_values(const Launch &L, const int *fown, const int *fa, long lon
         note_launch();
     }
 }
+
+void launch_sgs_sell_pos(const Launch &L, long long nops, const int *own, int *ent,
+                         const int *Ap, const int *sell_ptr) {
+    if (nops <= 0) return;
+    k_sgs_sell_pos<<<grid_for(nops, L.grid_rows), kBlock, 0, L.stream>>>(nops, own, ent, Ap,
+                                                                          sell_ptr);
+    note_launch();
+}
+
+template <class T>
+void launch_sgs_values_sell(const Launch &L, long long nops, const int *own, const int *pos,
+                            const T *sa, const uint2 *spk, T *val) {
+    if (nops <= 0) return;
+    k_sgs_values_sell<T><<<grid_for(nops, L.grid_rows), kBlock, 0, L.stream>>>(nops, own, pos,
+                                                                              sa, spk, val);
+    note_launch();
+}
+template void launch_sgs_values_sell<float>(const Launch &, long long, const int *, const int *,
+                                            const float *, const uint2 *, float *);
+template void launch_sgs_values_sell<double>(const Launch &, long long, const int *,
+                                             const int *, const double *, const uint2 *,
+                                             double *);
 
 namespace {
 // a kernel instantiation with its launch shape: `slot` bytes of shared
