@@ -244,16 +244,14 @@ __device__ __forceinline__ void cp_async_wait_all() {
     asm volatile("cp.async.wait_all;\n" ::: "memory");
 }
 
+__host__ __device__ __forceinline__ int pad4(int x) { return (x + 3) & ~3; }
+
 // The C coupling terms of one row: acc - sum_k v_k u_(src_k), with the
-// coupling words (local row | value index << 16) read from shared memory as
-// warp-uniform (broadcast) loads; ul and svl are u and the values offset by
-// the lane.
+// coupling words (local row | value index << 16) already in registers; ul
+// and svl are u and the values offset by the lane.
 template <class T, int C, bool CK>
-__device__ __forceinline__ T row_terms(const unsigned *cw, const T *ul, const T *svl, T acc, int m,
-                                       int nv, int &bad) {
-    unsigned w[C];
-#pragma unroll
-    for (int k = 0; k < C; ++k) w[k] = cw[k];
+__device__ __forceinline__ T row_terms(const unsigned (&w)[C], const T *ul, const T *svl, T acc,
+                                       int m, int nv, int &bad) {
     T va[C], ua[C];
 #pragma unroll
     for (int k = 0; k < C; ++k) {
@@ -269,12 +267,14 @@ __device__ __forceinline__ T row_terms(const unsigned *cw, const T *ul, const T 
 // (row t of lane L at u[32 t + L], conflict-free) with the coupling values
 // in sv (coupling o of lane L at sv[32 o + L]) and the class's sweep
 // structure in shared memory.  The rows of a level are spread over the
-// CTA's warps; a row's record (t | count << 10 | first coupling << 16) and
-// its couplings are the same for every lane.  Rows without couplings are not
-// listed.  One CTA barrier per level.
+// CTA's warps; a row's record is one 16-byte word, the same for every lane
+// (a broadcast load): t | count << 10 | first coupling << 16, then its first
+// three couplings (local row | value index << 16); the others are read from
+// the coupling words.  Rows without couplings are not listed.  One CTA
+// barrier per level.
 template <class T, int NW, bool CK>
 __device__ __forceinline__ void batch_sweep(T *u, const T *sv, int nl, const unsigned *lvl,
-                                            const unsigned *rec, const unsigned *cpl, int nr,
+                                            const uint4 *rec, const unsigned *cpl, int nr,
                                             int m, int nv, int warp, int lane, int &bad) {
     T *ul = u + lane;
     const T *svl = sv + lane;
@@ -285,25 +285,32 @@ __device__ __forceinline__ void batch_sweep(T *u, const T *sv, int nl, const uns
             a = e = 0;
         }
         for (int x = a + warp; x < e; x += NW) {
-            const unsigned r = rec[x];
-            const int cnt = (int)((r >> 10) & 63u), c0 = (int)(r >> 16);
+            const uint4 r = rec[x];
+            const int cnt = (int)((r.x >> 10) & 63u), c0 = (int)(r.x >> 16);
             if (CK && c0 + cnt > nv) {
                 bad = 1;
                 continue;
             }
-            const int t = chk_index<CK>((int)(r & 1023u), m, bad);
-            const unsigned *cw = cpl + c0;
+            const int t = chk_index<CK>((int)(r.x & 1023u), m, bad);
             T acc = ul[32 * t];
             switch (cnt) {  // warp-uniform: exact unrolled paths for short rows
-                case 1: acc = row_terms<T, 1, CK>(cw, ul, svl, acc, m, nv, bad); break;
-                case 2: acc = row_terms<T, 2, CK>(cw, ul, svl, acc, m, nv, bad); break;
-                case 3: acc = row_terms<T, 3, CK>(cw, ul, svl, acc, m, nv, bad); break;
-                case 4: acc = row_terms<T, 4, CK>(cw, ul, svl, acc, m, nv, bad); break;
+                case 1: {
+                    const unsigned w[1] = {r.y};
+                    acc = row_terms<T, 1, CK>(w, ul, svl, acc, m, nv, bad);
+                    break;
+                }
+                case 2: {
+                    const unsigned w[2] = {r.y, r.z};
+                    acc = row_terms<T, 2, CK>(w, ul, svl, acc, m, nv, bad);
+                    break;
+                }
                 default: {
-                    int k = 0;
-                    for (; k + 4 <= cnt; k += 4)
-                        acc = row_terms<T, 4, CK>(cw + k, ul, svl, acc, m, nv, bad);
-                    for (; k < cnt; ++k) acc = row_terms<T, 1, CK>(cw + k, ul, svl, acc, m, nv, bad);
+                    const unsigned w[3] = {r.y, r.z, r.w};
+                    acc = row_terms<T, 3, CK>(w, ul, svl, acc, m, nv, bad);
+                    for (int k = 3; k < cnt; ++k) {
+                        const unsigned wk[1] = {cpl[c0 + k]};
+                        acc = row_terms<T, 1, CK>(wk, ul, svl, acc, m, nv, bad);
+                    }
                 }
             }
             ul[32 * t] = acc;
@@ -359,7 +366,8 @@ k_sgs_batch(int b0, int b1, const int *__restrict__ bat_hdr, const int *__restri
         if constexpr (CK) {
             // a batch whose header or class does not fit the arrays and the
             // shared memory is skipped whole (the same test in every thread)
-            const long long words = (long long)nlf + 1 + nrf + nv + nlb + 1 + nrb + nv;
+            const long long words = pad4(nlf + 1) + 4LL * nrf + pad4(nv) + pad4(nlb + 1) + 4LL * nrb +
+                                    pad4(nv);
             if (m < 0 || nv < 0 || nlf < 0 || nlb < 0 || nrf < 0 || nrb < 0 || off < 0 ||
                 (off & 3) || wpad < words || (wpad & 3) || wpad > wmax || r0 < 0 || v0 < 0 ||
                 m > umax || nv > vmax || off + wpad > nblob ||
@@ -409,9 +417,11 @@ k_sgs_batch(int b0, int b1, const int *__restrict__ bat_hdr, const int *__restri
         __syncthreads();
         if (s_abort) break;
         const unsigned *fl = sb;
-        const unsigned *fr = fl + nlf + 1, *fc = fr + nrf;
-        const unsigned *bl = fc + nv;
-        const unsigned *br = bl + nlb + 1, *bc = br + nrb;
+        const uint4 *fr = reinterpret_cast<const uint4 *>(fl + pad4(nlf + 1));
+        const unsigned *fc = reinterpret_cast<const unsigned *>(fr + nrf);
+        const unsigned *bl = fc + pad4(nv);
+        const uint4 *br = reinterpret_cast<const uint4 *>(bl + pad4(nlb + 1));
+        const unsigned *bc = reinterpret_cast<const unsigned *>(br + nrb);
         batch_sweep<T, NW, CK>(u, sv, nlf, fl, fr, fc, nrf, m, nv, warp, lane, bad);
         if (gmode != SG_NONE) {
             // a thread's squares of one batch in T (a few dozen terms; the
@@ -667,7 +677,7 @@ int build_sgs_plan(int n, int nc, const int *Ap, const int *Aj, const int *Pp, c
             const int m = colp[gcol[g] + 1] - colp[gcol[g]];
             if (gsize[g] != 1 || m > kBatchRows) continue;
             lists(g, loc, L);
-            if (128LL * (m + L.nf) + 4LL * (4LL * m + 2 * L.nf + 16) > kBatchSmem || L.nf > 65535)
+            if (128LL * (m + L.nf) + 4LL * (10LL * m + 2 * L.nf + 16) > kBatchSmem || L.nf > 65535)
                 continue;
             std::vector<int> tcnt(m, 0);
             bool fits = true;
@@ -734,7 +744,7 @@ int build_sgs_plan(int n, int nc, const int *Ap, const int *Aj, const int *Pp, c
         // class with the most groups, then the rest
         auto foot = [&](int b) {
             const long long m = (long long)canon[b].rows.size(), nv = canon[b].nf;
-            return 128LL * (m + nv) + 4LL * (4 * m + 2 * nv + 16);  // u, values, structure
+            return 128LL * (m + nv) + 4LL * (10 * m + 2 * nv + 16);  // u, values, structure
         };
         auto per_sm = [](long long bytes) {
             const long long cap = 228LL * 1024, per = bytes + 1024 + 512;
@@ -784,17 +794,24 @@ int build_sgs_plan(int n, int nc, const int *Ap, const int *Aj, const int *Pp, c
                 for (int l = 1; l <= maxl; ++l) {
                     for (int t : rows_at[l]) {
                         const int cnt = sw == 0 ? (int)L.lo[t].size() : (int)tr[t].size();
-                        rec.push_back((unsigned)t | (unsigned)cnt << 10 | (unsigned)cpl.size() << 16);
+                        unsigned r4[4] = {(unsigned)t | (unsigned)cnt << 10 | (unsigned)cpl.size() << 16,
+                                          0u, 0u, 0u};
                         for (int x = 0; x < cnt; ++x) {
                             const int src = sw == 0 ? L.lo[t][x] : tr[t][x].first;
                             const int vi = sw == 0 ? fstart[t] + x : tr[t][x].second;
-                            cpl.push_back((unsigned)src | (unsigned)vi << 16);
+                            const unsigned w = (unsigned)src | (unsigned)vi << 16;
+                            if (x < 3) r4[1 + x] = w;
+                            cpl.push_back(w);
                         }
+                        rec.insert(rec.end(), r4, r4 + 4);
                     }
-                    lvl.push_back((unsigned)rec.size());
+                    lvl.push_back((unsigned)(rec.size() / 4));
                 }
                 nl[sw] = maxl;
-                nr[sw] = (int)rec.size();
+                nr[sw] = (int)(rec.size() / 4);
+                // 16-byte aligned regions: level bounds, records, coupling words
+                while (lvl.size() % 4) lvl.push_back(0u);
+                while (cpl.size() % 4) cpl.push_back(0u);
                 for (auto *v : {&lvl, &rec, &cpl}) out.cls_blob.insert(out.cls_blob.end(), v->begin(), v->end());
             }
             while (out.cls_blob.size() % 4) out.cls_blob.push_back(0u);
