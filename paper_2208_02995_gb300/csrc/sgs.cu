@@ -45,7 +45,7 @@ constexpr int kBatchRows = 1024;      // rows of a batched group (10-bit local r
 constexpr int kBatchRowCpl = 63;      // couplings of one row in one sweep (6-bit counts)
 constexpr int kBatchMin = 8;          // groups of one structure before it is batched
 constexpr int kBatchTail = 1024;      // rarer structures batched too while this few groups have them
-constexpr long long kBatchSmem = 100 * 1024;  // float bytes of one batch (u and values, 32 lanes)
+constexpr long long kBatchSmem = 100 * 1024;  // float bytes of one batch (u, values, structure)
 constexpr int kSgsWaitLimit = 1 << 22;        // bounded wait for a batch's copies
 constexpr int kGatherRows = 16;               // rows per warp whose loads are issued together
 
