@@ -269,13 +269,14 @@ __device__ __forceinline__ T row_terms(const unsigned (&w)[C], const T *ul, cons
 // structure in shared memory.  The rows of a level are spread over the
 // CTA's warps; a row's record is one 16-byte word, the same for every lane
 // (a broadcast load): t | count << 10 | first coupling << 16, then its first
-// three couplings (local row | value index << 16); the others are read from
-// the coupling words.  Rows without couplings are not listed.  One CTA
+// three couplings (local row | value index << 16); a row with more reads the
+// rest from the spill words, from the record's first-coupling index on.  Rows without couplings are not listed.  One CTA
 // barrier per level.
 template <class T, int NW, bool CK>
 __device__ __forceinline__ void batch_sweep(T *u, const T *sv, int nl, const unsigned *lvl,
                                             const uint4 *rec, const unsigned *cpl, int nr,
-                                            int m, int nv, int warp, int lane, int &bad) {
+                                            int nspill, int m, int nv, int warp, int lane,
+                                            int &bad) {
     T *ul = u + lane;
     const T *svl = sv + lane;
     for (int l = 0; l < nl; ++l) {
@@ -287,7 +288,7 @@ __device__ __forceinline__ void batch_sweep(T *u, const T *sv, int nl, const uns
         for (int x = a + warp; x < e; x += NW) {
             const uint4 r = rec[x];
             const int cnt = (int)((r.x >> 10) & 63u), c0 = (int)(r.x >> 16);
-            if (CK && c0 + cnt > nv) {
+            if (CK && cnt > 3 && c0 + cnt - 3 > nspill) {
                 bad = 1;
                 continue;
             }
@@ -308,7 +309,7 @@ __device__ __forceinline__ void batch_sweep(T *u, const T *sv, int nl, const uns
                     const unsigned w[3] = {r.y, r.z, r.w};
                     acc = row_terms<T, 3, CK>(w, ul, svl, acc, m, nv, bad);
                     for (int k = 3; k < cnt; ++k) {
-                        const unsigned wk[1] = {cpl[c0 + k]};
+                        const unsigned wk[1] = {cpl[c0 + k - 3]};
                         acc = row_terms<T, 1, CK>(wk, ul, svl, acc, m, nv, bad);
                     }
                 }
@@ -361,13 +362,14 @@ k_sgs_batch(int b0, int b1, const int *__restrict__ bat_hdr, const int *__restri
         const int *h = bat_hdr + 4 * (size_t)b;
         const int c = h[0], r0 = h[1], v0 = h[2];
         const int *ch = cls_hdr + 8 * (size_t)c;
-        const int m = ch[0], nv = ch[1], nlf = ch[2], nlb = ch[3], off = ch[4], nrf = ch[5],
-                  nrb = ch[6], wpad = ch[7];
+        const int m = ch[0], nv = ch[1], nlf = ch[2] & 0xffff, nlb = ch[2] >> 16,
+                  nsf = ch[3] & 0xffff, nsb = ch[3] >> 16, off = ch[4], nrf = ch[5], nrb = ch[6],
+                  wpad = ch[7];
         if constexpr (CK) {
             // a batch whose header or class does not fit the arrays and the
             // shared memory is skipped whole (the same test in every thread)
-            const long long words = pad4(nlf + 1) + 4LL * nrf + pad4(nv) + pad4(nlb + 1) + 4LL * nrb +
-                                    pad4(nv);
+            const long long words = pad4(nlf + 1) + 4LL * nrf + pad4(nsf) + pad4(nlb + 1) +
+                                    4LL * nrb + pad4(nsb);
             if (m < 0 || nv < 0 || nlf < 0 || nlb < 0 || nrf < 0 || nrb < 0 || off < 0 ||
                 (off & 3) || wpad < words || (wpad & 3) || wpad > wmax || r0 < 0 || v0 < 0 ||
                 m > umax || nv > vmax || off + wpad > nblob ||
@@ -419,10 +421,10 @@ k_sgs_batch(int b0, int b1, const int *__restrict__ bat_hdr, const int *__restri
         const unsigned *fl = sb;
         const uint4 *fr = reinterpret_cast<const uint4 *>(fl + pad4(nlf + 1));
         const unsigned *fc = reinterpret_cast<const unsigned *>(fr + nrf);
-        const unsigned *bl = fc + pad4(nv);
+        const unsigned *bl = fc + pad4(nsf);
         const uint4 *br = reinterpret_cast<const uint4 *>(bl + pad4(nlb + 1));
         const unsigned *bc = reinterpret_cast<const unsigned *>(br + nrb);
-        batch_sweep<T, NW, CK>(u, sv, nlf, fl, fr, fc, nrf, m, nv, warp, lane, bad);
+        batch_sweep<T, NW, CK>(u, sv, nlf, fl, fr, fc, nrf, nsf, m, nv, warp, lane, bad);
         if (gmode != SG_NONE) {
             // a thread's squares of one batch in T (a few dozen terms; the
             // FP64 pipe is slow), then one double addition per batch
@@ -431,7 +433,7 @@ k_sgs_batch(int b0, int b1, const int *__restrict__ bat_hdr, const int *__restri
             g += (double)gb;
             __syncthreads();  // every warp has read u before the backward sweep rewrites it
         }
-        batch_sweep<T, NW, CK>(u, sv, nlb, bl, br, bc, nrb, m, nv, warp, lane, bad);
+        batch_sweep<T, NW, CK>(u, sv, nlb, bl, br, bc, nrb, nsb, m, nv, warp, lane, bad);
         for (int t0 = warp; t0 < m; t0 += kGatherRows * NW) {
             int p[kGatherRows];
 #pragma unroll
@@ -740,26 +742,6 @@ int build_sgs_plan(int n, int nc, const int *Ap, const int *Aj, const int *Pp, c
             lists(cls_rep[c], loc, canon.back());
         }
         const int nbc = (int)canon.size();
-        // buckets: the classes whose batch fits as many CTAs per SM as the
-        // class with the most groups, then the rest
-        auto foot = [&](int b) {
-            const long long m = (long long)canon[b].rows.size(), nv = canon[b].nf;
-            return 128LL * (m + nv) + 4LL * (10 * m + 2 * nv + 16);  // u, values, structure
-        };
-        auto per_sm = [](long long bytes) {
-            const long long cap = 228LL * 1024, per = bytes + 1024 + 512;
-            return std::min<long long>(2048 / (32 * kSgsWarps), cap / per);
-        };
-        std::vector<int> bucket_of(nbc, 0);
-        if (nbc > 0) {
-            int dom = 0;
-            for (int b = 1; b < nbc; ++b)
-                if (cls_count[bc_src[b]] > cls_count[bc_src[dom]]) dom = b;
-            long long fa = 0;
-            for (int b = 0; b < nbc; ++b)
-                if (per_sm(foot(b)) >= per_sm(foot(dom))) fa = std::max(fa, foot(b));
-            for (int b = 0; b < nbc; ++b) bucket_of[b] = foot(b) <= fa ? 0 : 1;
-        }
         // class sweep structures: levels of the rows with couplings, row
         // records and coupling words (see batch_sweep), 16-byte aligned and
         // padded; value o of a class is its o-th lower coupling in row order
@@ -781,7 +763,7 @@ int build_sgs_plan(int n, int nc, const int *Ap, const int *Aj, const int *Pp, c
                 for (auto &pr : tr[t]) bl[t] = std::max(bl[t], bl[pr.first] + 1);
             while (out.cls_blob.size() % 4) out.cls_blob.push_back(0u);
             const int off = (int)out.cls_blob.size();
-            int nl[2] = {0, 0}, nr[2] = {0, 0};
+            int nl[2] = {0, 0}, nr[2] = {0, 0}, ns[2] = {0, 0};
             for (int sw = 0; sw < 2; ++sw) {
                 const std::vector<int> &lev = sw == 0 ? fl : bl;
                 int maxl = 0;
@@ -801,7 +783,7 @@ int build_sgs_plan(int n, int nc, const int *Ap, const int *Aj, const int *Pp, c
                             const int vi = sw == 0 ? fstart[t] + x : tr[t][x].second;
                             const unsigned w = (unsigned)src | (unsigned)vi << 16;
                             if (x < 3) r4[1 + x] = w;
-                            cpl.push_back(w);
+                            else cpl.push_back(w);  // spill: couplings past the third
                         }
                         rec.insert(rec.end(), r4, r4 + 4);
                     }
@@ -809,6 +791,7 @@ int build_sgs_plan(int n, int nc, const int *Ap, const int *Aj, const int *Pp, c
                 }
                 nl[sw] = maxl;
                 nr[sw] = (int)(rec.size() / 4);
+                ns[sw] = (int)cpl.size();
                 // 16-byte aligned regions: level bounds, records, coupling words
                 while (lvl.size() % 4) lvl.push_back(0u);
                 while (cpl.size() % 4) cpl.push_back(0u);
@@ -816,8 +799,29 @@ int build_sgs_plan(int n, int nc, const int *Ap, const int *Aj, const int *Pp, c
             }
             while (out.cls_blob.size() % 4) out.cls_blob.push_back(0u);
             const int wpad = (int)out.cls_blob.size() - off;
-            const int h[8] = {m, nv, nl[0], nl[1], off, nr[0], nr[1], wpad};
+            // level counts (< 1024) and spill counts (< 65536) packed in pairs
+            const int h[8] = {m, nv, nl[0] | nl[1] << 16, ns[0] | ns[1] << 16, off, nr[0], nr[1], wpad};
             out.cls_hdr.insert(out.cls_hdr.end(), h, h + 8);
+        }
+        // buckets: the classes whose batch fits as many CTAs per SM as the
+        // class with the most groups, then the rest
+        auto foot = [&](int b) {  // u, values and the class's sweep structure
+            return 128LL * ((long long)canon[b].rows.size() + canon[b].nf) +
+                   4LL * out.cls_hdr[8 * (size_t)b + 7];
+        };
+        auto per_sm = [](long long bytes) {
+            const long long cap = 228LL * 1024, per = bytes + 1024 + 512;
+            return std::min<long long>(2048 / (32 * kSgsWarps), cap / per);
+        };
+        std::vector<int> bucket_of(nbc, 0);
+        if (nbc > 0) {
+            int dom = 0;
+            for (int b = 1; b < nbc; ++b)
+                if (cls_count[bc_src[b]] > cls_count[bc_src[dom]]) dom = b;
+            long long fa = 0;
+            for (int b = 0; b < nbc; ++b)
+                if (per_sm(foot(b)) >= per_sm(foot(dom))) fa = std::max(fa, foot(b));
+            for (int b = 0; b < nbc; ++b) bucket_of[b] = foot(b) <= fa ? 0 : 1;
         }
         // batches by bucket, then by class, groups in column order
         std::vector<int> cls_first_batch(nbc, 0);
